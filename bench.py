@@ -1,0 +1,313 @@
+"""Benchmark: insert + deleteMin throughput of the generalized concurrent heap.
+
+Workload (one step): the raw heap throughput configuration of arXiv 1906.06504
+Section 5.2 at GB300 scale -- 2^26 uniform uint32 keys, node capacity k = 1024,
+inserted into an empty heap and then all deleted (insert-all, deleteMin-all),
+every thread block of the device running operations concurrently.
+
+value  : (keys inserted + keys deleted) / device time, inputs resident in HBM.
+e2e    : the same through the C ABI from pinned host buffers, the H2D copy of
+         the keys and the D2H copy of the sorted output inside the timed region.
+roofline: algorithmic node bytes of the dominant launch (deleteMin-all) over
+         its CUDA-event duration, against the measured HBM copy bandwidth.
+cpu_baseline: the CPU oracle (sequential binary heap) on a bounded sample.
+
+--impl reference times that CPU oracle as the reference arm.
+Multi-GPU (torchrun): every rank drives its own heap (independent replicas;
+a single heap has one root and does not shard), weak scaling.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_KEYS = 1 << 26
+K = 1024
+METRIC = "insert+deleteMin keys/s (k=1024, 2^26 u32)"
+UNIT = "keys/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(n_sample):
+    """Insert-all then delete-all of n_sample keys through the oracle's
+    binary heap; returns (keys/s, seconds)."""
+    import oracle
+    from paper_1906_06504_gb300 import inputs
+    keys = inputs.keys_u32(inputs.config_seed(2), n_sample)
+    q = oracle.BinaryHeapPQ(n_sample)
+    t0 = time.perf_counter()
+    q.push(keys)
+    out = q.pop(n_sample, dtype=np.uint32)
+    dt = time.perf_counter() - t0
+    q.close()
+    assert out.size == n_sample
+    return 2 * n_sample / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    n_sample = 1 << 21
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt = cpu_oracle_sample(n_sample)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "insert-all + deleteMin-all, uniform u32 keys, k=1024",
+                   "keys": N_KEYS, "k": K, "sample_keys": n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "insert-all + delete-all of 2^21 of the same uniform keys "
+                                   "per step, sequential binary heap, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_gpu(args):
+    import torch
+    from paper_1906_06504_gb300 import build, inputs
+    build.build()
+    from paper_1906_06504_gb300.heap import GHeap
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, k = args.keys, args.k
+    keys_np = inputs.keys_u32(inputs.config_seed(2) + rank, n)
+    keys = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    heap = GHeap(capacity=n, k=k)
+    heap.set_launch(ctas=args.ctas, items_per_thread=args.ipt)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        heap.insert(keys)
+        if ev is not None:
+            ev[1].record(stream)
+        heap.delete_min(n, out=out, count=cnt)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    heap.sync()
+    # correctness of the timed configuration (cheap property check)
+    assert int(cnt.item()) == n
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            step(evs[i])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    heap.sync()
+    ms = t_start.elapsed_time(t_end)
+    ins_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    del_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = 2.0 * n * args.steps * ws / (ms / 1e3)
+
+    # node traffic of one step, counted by the kernel (separate untimed run)
+    cheap = GHeap(capacity=n, k=k, stats=True)
+    cheap.set_launch(ctas=args.ctas, items_per_thread=args.ipt)
+    cheap.insert(keys)
+    cheap.sync()
+    st_ins = cheap.stats()
+    cheap.delete_min(n, out=out, count=cnt)
+    cheap.sync()
+    st_all = cheap.stats()
+    cheap.close()
+    st_del = {a: st_all[a] - st_ins[a] for a in st_all}
+    node_b = k * 4
+    del_bytes = (st_del["node_loads"] + st_del["node_stores"]) * node_b + n * 4
+    ins_bytes = (st_ins["node_loads"] + st_ins["node_stores"]) * node_b + n * 4
+    del_avg_ms = float(np.mean(del_ms))
+    ins_avg_ms = float(np.mean(ins_ms))
+    dom = "delete" if del_avg_ms >= ins_avg_ms else "insert"
+    dom_bytes, dom_ms = (del_bytes, del_avg_ms) if dom == "delete" else (ins_bytes, ins_avg_ms)
+    peak, peak_kind = peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+
+    # end to end through the C ABI from pinned host memory
+    host_in = torch.from_numpy(keys_np.view(np.int32)).pin_memory()
+    host_out = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    heap.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        keys.copy_(host_in, non_blocking=True)
+        heap.insert(keys)
+        heap.delete_min(n, out=out, count=cnt)
+        host_out.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    assert np.array_equal(host_out.numpy().view(np.uint32)[:1024], np.sort(keys_np)[:1024])
+    e2e_value = 2.0 * n * e2e_steps * ws / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_sample = 1 << 22
+        v, dt = cpu_oracle_sample(n_sample)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "insert-all + delete-all of the first 2^22 keys of the same seeded "
+                         "uniform stream, sequential binary heap, %.1f s" % dt}
+
+    heap.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
+                       "keys": n, "k": k, "threads_per_block": 2 * k // args.ipt,
+                       "ctas": args.ctas or "device-filling",
+                       "l2": "inputs and heap (256 MB each) exceed the 126 MB L2",
+                       "insert_ms": ins_avg_ms, "delete_ms": del_avg_ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "heap_kernel (%s-all launch)" % dom,
+                         "algorithmic_bytes": dom_bytes},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 4,
+                    "d2h_bytes_per_step": n * 4},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "stats_delete": st_del, "stats_insert": st_ins,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--keys", type=int, default=N_KEYS)
+    ap.add_argument("--k", type=int, default=K)
+    ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--ipt", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

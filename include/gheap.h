@@ -1,0 +1,175 @@
+/*
+ * gheap.h -- C ABI of the GB300 generalized concurrent heap.
+ *
+ * Implements the TD-INS/TD-DEL concurrent heap of "Accelerating Concurrent
+ * Heap on GPUs" (Chen, Hua, Huang, Bierema, Zhang, Zhang; arXiv 1906.06504):
+ * a min-heap whose nodes each hold k sorted keys (Section 3.1), insert and
+ * deleteMin as top-down walks that MergeAndSort one k-batch per level
+ * (Section 3.2), per-node multi-state locks taken parent before child
+ * (Section 3.3.1), a partial buffer at the root for batches smaller than k
+ * (Section 3.3.2) and bit-reversal target placement (Section 4.3).  Every
+ * operation runs on one thread block of a persistent CUDA kernel; the whole
+ * heap lives in device memory.
+ *
+ * Conventions for every entry point:
+ *   - Return value: GHEAP_OK (0) or a negative GHEAP_ERR_* code.
+ *   - Key buffers passed in are DEVICE pointers owned by the caller, holding
+ *     `key_bytes`-wide unsigned integers (uint32_t or uint64_t) in native
+ *     byte order; they must stay valid until the work enqueued on `stream`
+ *     has finished.  Heap memory is owned by the library.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously and ordered on that stream.
+ *   - Device-side failures (a lock wait that gave up, GHEAP_ERR_TIMEOUT; an
+ *     insert past the node storage, GHEAP_ERR_FULL) are sticky: they are
+ *     reported by heap_sync() and by every later call on the same heap, and
+ *     the heap must then be reset or destroyed.
+ *   - A heap may be used from one host thread at a time.
+ */
+#ifndef GHEAP_H
+#define GHEAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gheap_s *gheap_t;
+
+#define GHEAP_OK 0
+#define GHEAP_ERR_ARG (-1)     /* bad argument: null pointer, k, key_bytes */
+#define GHEAP_ERR_OOM (-2)     /* device allocation failed                 */
+#define GHEAP_ERR_FULL (-3)    /* insert would exceed capacity_keys        */
+#define GHEAP_ERR_TIMEOUT (-4) /* a bounded lock wait gave up (sticky)     */
+#define GHEAP_ERR_CUDA (-5)    /* a CUDA runtime call failed               */
+#define GHEAP_ERR_STATE (-6)   /* device found an impossible node state    */
+
+/* heap_create flags */
+#define GHEAP_FLAG_STATS 1u    /* count node loads/stores and merges       */
+
+/* One entry of the linearization record (Section 3.3.3): the operation that
+ * held the root lock in that position.  kind_n = (kind << 24) | n with kind
+ * GHEAP_OP_INS or GHEAP_OP_DEL and n the keys inserted or returned.  `ref` is
+ * the input key offset of an insert chunk (heap_insert), the output key
+ * offset of a delete (heap_delete_min), or the op index (heap_ops). */
+typedef struct {
+    uint32_t call_id;
+    uint32_t kind_n;
+    uint64_t ref;
+} gheap_log_entry;
+
+#define GHEAP_OP_INS 1u
+#define GHEAP_OP_DEL 2u
+
+/* One operation of heap_ops.  INS: insert n (1..k) keys read from
+ * in_keys[offset .. offset+n).  DEL: delete up to n (1..k) smallest keys and
+ * write them ascending to out_keys[offset ..); the count goes to
+ * out_counts[i]. */
+typedef struct {
+    uint32_t kind;
+    uint32_t n;
+    uint64_t offset;
+} gheap_op;
+
+/* Creates an empty heap able to hold `capacity_keys` keys in nodes of `k`
+ * keys (Section 3.1: node i occupies keys [i*k, (i+1)*k) of one array).
+ * k: a power of two in [1, 2048].  key_bytes: 4 or 8.  flags: GHEAP_FLAG_*.
+ * log_capacity: number of linearization-record entries kept (0 = none).
+ * Allocates all device memory on the current CUDA device; errors: ARG, OOM,
+ * CUDA. */
+int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k,
+                uint32_t key_bytes, uint32_t flags, uint64_t log_capacity);
+
+/* Frees the heap and its device memory (synchronizes the device first). */
+int heap_destroy(gheap_t h);
+
+/* Launch shape of the persistent kernels: `ctas` thread blocks (0 = as many
+ * as fit on the device at once) of 2k/items_per_thread threads (at least 32,
+ * at most 512), items_per_thread in {2, 4, 8}.  The paper's best setting is
+ * k = 1024 with 512 threads (Section 5.4), i.e. items_per_thread = 4, the
+ * default. */
+int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread);
+
+/* Bound on every lock wait, in nanoseconds (default 2e9).  A wait that runs
+ * out sets the sticky GHEAP_ERR_TIMEOUT and the kernel returns. */
+int heap_set_timeout(gheap_t h, uint64_t ns);
+
+/* Inserts n keys (Section 3.2.2 top-down INS, Section 3.3.2 partial
+ * buffer).  The keys are split into ceil(n/k) INS operations of consecutive
+ * chunks of k (the last may be partial), run concurrently by the persistent
+ * thread blocks.  Returns GHEAP_ERR_FULL, and enqueues nothing, when the
+ * heap could exceed capacity_keys. */
+int heap_insert(gheap_t h, const void *d_keys, uint64_t n, void *stream);
+
+/* Deletes the min(n, size) smallest keys (Section 3.2.1 DEL) as ceil(n/k)
+ * DEL operations and writes them to d_out in the order the operations held
+ * the root, which is ascending when no insert runs concurrently.  When
+ * d_count is not NULL it receives (device uint64_t) the number written. */
+int heap_delete_min(gheap_t h, void *d_out, uint64_t n, uint64_t *d_count,
+                    void *stream);
+
+/* Runs an arbitrary list of INS/DEL operations concurrently (the mixed
+ * insert/delete workload of Section 5.5).  d_ops: device array of n_ops
+ * gheap_op.  max_insert_keys: the caller's bound on the keys the list
+ * inserts, used for the capacity check.  d_out_counts: device uint32_t per
+ * op (DEL: keys returned; INS: n), may be NULL. */
+int heap_ops(gheap_t h, const gheap_op *d_ops, uint64_t n_ops,
+             const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
+             uint64_t max_insert_keys, void *stream);
+
+/* Waits for all work on the heap's last stream and returns its sticky device
+ * error, if any. */
+int heap_sync(gheap_t h);
+
+/* Number of keys in the heap (synchronizes). */
+int heap_size(gheap_t h, uint64_t *out);
+
+/* Empties the heap, clears its linearization record and any sticky error
+ * (enqueued on `stream`). */
+int heap_reset(gheap_t h, void *stream);
+
+/* Copies up to `cap` linearization-record entries to host memory, in root
+ * order, and the total number of operations recorded so far to *n_total
+ * (synchronizes).  Entries beyond log_capacity are not kept. */
+int heap_get_log(gheap_t h, gheap_log_entry *host_buf, uint64_t cap,
+                 uint64_t *n_copied, uint64_t *n_total);
+
+/* Copies a quiescent heap to host memory (synchronizes): host_keys receives
+ * (max_nodes+1)*k keys indexed by storage slot, host_state (max_nodes+1)
+ * uint32_t node states (1 = occupied), host_buf k keys (the partial buffer),
+ * hdr[0] = full nodes, hdr[1] = partial-buffer keys, hdr[2] = operations
+ * recorded.  Storage slot j holds the j-th allocated node, whose tree
+ * position is given by heap_slot_to_node().  Any pointer may be NULL. */
+int heap_snapshot(gheap_t h, void *host_keys, uint32_t *host_state,
+                  void *host_buf, uint64_t *hdr);
+
+/* Shape queries: node capacity in nodes (max_nodes) and k. */
+int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k,
+                  uint32_t *key_bytes);
+
+/* Tree position (1-based, children of p are 2p and 2p+1) of storage slot
+ * j >= 1: the bit-reversal permutation within the slot's level
+ * (Section 4.3).  The map is its own inverse. */
+uint64_t heap_slot_to_node(uint64_t j);
+
+/* Device counters when created with GHEAP_FLAG_STATS (synchronizes):
+ * out[0] node loads, out[1] node stores, out[2] merges, out[3] merges skipped
+ * as disjoint (Section 4.3), out[4] INS ops, out[5] DEL ops, out[6] lock
+ * waits that spun, out[7] sum of root-hold time in ns.  n <= 8. */
+int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
+
+/* Test hook for the bounded waits: marks the root lock as held, with no
+ * holder that will ever release it, so that every later operation's wait
+ * runs out (GHEAP_ERR_TIMEOUT after the heap_set_timeout bound) instead of
+ * completing.  The paper has no counterpart; heap_reset() undoes it. */
+int heap_debug_hold_root(gheap_t h, void *stream);
+
+/* Human-readable text of an error code. */
+const char *heap_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GHEAP_H */

@@ -1,0 +1,433 @@
+// gheap.cu -- C ABI of the GB300 generalized concurrent heap (include/gheap.h).
+//
+// Host side: device memory layout, launch shapes, capacity accounting and
+// error reporting.  All heap arithmetic runs in the persistent kernel of
+// gheap_kernel.cuh (TD-INS/TD-DEL heap of arXiv 1906.06504, Sections 3-4).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gheap.h"
+#include "gheap_kernel.cuh"
+
+struct gheap_s {
+    int device;
+    uint32_t k;
+    uint32_t key_bytes;
+    uint32_t flags;
+    uint64_t capacity;       // keys
+    uint32_t max_nodes;      // storage slots 1..max_nodes
+    void *d_keys;
+    uint32_t *d_state;
+    void *d_buf;
+    gh::Hdr *d_hdr;
+    gh::Ctl *d_ctl;
+    gheap_log_entry *d_log;
+    uint64_t log_cap;
+    unsigned long long *d_stats;
+    uint32_t ctas;           // 0 = fill the device
+    uint32_t ipt;            // merge outputs per thread: 2, 4 or 8
+    uint64_t timeout_ns;
+    int sm_count;
+    int sticky;              // host copy of a sticky device error
+    uint64_t size_upper;     // upper bound on the keys held
+    uint32_t call_id;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? GHEAP_OK : GHEAP_ERR_CUDA; }
+
+int map_dev_err(uint32_t e)
+{
+    switch (e) {
+    case gh::E_NONE: return GHEAP_OK;
+    case gh::E_TIMEOUT: return GHEAP_ERR_TIMEOUT;
+    case gh::E_FULL: return GHEAP_ERR_FULL;
+    default: return GHEAP_ERR_STATE;
+    }
+}
+
+uint32_t threads_for(uint32_t k, uint32_t ipt)
+{
+    uint32_t t = 2 * k / ipt;
+    if (t < 32) t = 32;
+    return t;
+}
+
+template <typename K, int IPT>
+int launch_t(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
+{
+    auto kern = gh::heap_kernel<K, IPT>;
+    const uint32_t threads = threads_for(h->k, IPT);
+    const size_t smem = 4u * (size_t)h->k * sizeof(K);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
+    if (e != cudaSuccess || per_sm < 1) return GHEAP_ERR_CUDA;
+    uint64_t grid = h->ctas ? h->ctas : (uint64_t)per_sm * h->sm_count;
+    if (grid > (uint64_t)per_sm * h->sm_count) grid = (uint64_t)per_sm * h->sm_count;
+    if (grid > n_ops) grid = n_ops;
+    if (grid == 0) return GHEAP_OK;
+    e = cudaMemsetAsync(h->d_ctl, 0, sizeof(gh::Ctl), s);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    kern<<<(unsigned)grid, threads, smem, s>>>(p);
+    return cuda_err(cudaGetLastError());
+}
+
+template <typename K>
+int launch_k(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
+{
+    switch (h->ipt) {
+    case 2: return launch_t<K, 2>(h, p, n_ops, s);
+    case 4: return launch_t<K, 4>(h, p, n_ops, s);
+    case 8: return launch_t<K, 8>(h, p, n_ops, s);
+    default: return GHEAP_ERR_ARG;
+    }
+}
+
+template <typename K>
+gh::Params<K> base_params(gheap_t h, uint32_t mode)
+{
+    gh::Params<K> p;
+    memset(&p, 0, sizeof(p));
+    p.keys = static_cast<K *>(h->d_keys);
+    p.state = h->d_state;
+    p.buf = static_cast<K *>(h->d_buf);
+    p.hdr = h->d_hdr;
+    p.ctl = h->d_ctl;
+    p.log = h->d_log;
+    p.log_cap = h->log_cap;
+    p.stats = (h->flags & GHEAP_FLAG_STATS) ? h->d_stats : nullptr;
+    p.k = h->k;
+    p.max_nodes = h->max_nodes;
+    p.timeout_ns = h->timeout_ns;
+    p.mode = mode;
+    p.call_id = ++h->call_id;
+    return p;
+}
+
+int launch(gheap_t h, uint32_t mode, const void *in, void *out, uint64_t n,
+           const gheap_op *ops, uint64_t n_ops, uint32_t *out_counts, uint64_t *out_total,
+           cudaStream_t s)
+{
+    uint64_t launch_ops = mode == gh::MODE_OPS ? n_ops : (n + h->k - 1) / h->k;
+    if (h->key_bytes == 4) {
+        gh::Params<uint32_t> p = base_params<uint32_t>(h, mode);
+        p.in = static_cast<const uint32_t *>(in);
+        p.out = static_cast<uint32_t *>(out);
+        p.n = n;
+        p.ops = ops;
+        p.n_ops = n_ops;
+        p.out_counts = out_counts;
+        p.out_total = reinterpret_cast<unsigned long long *>(out_total);
+        return launch_k<uint32_t>(h, p, launch_ops, s);
+    } else {
+        gh::Params<uint64_t> p = base_params<uint64_t>(h, mode);
+        p.in = static_cast<const uint64_t *>(in);
+        p.out = static_cast<uint64_t *>(out);
+        p.n = n;
+        p.ops = ops;
+        p.n_ops = n_ops;
+        p.out_counts = out_counts;
+        p.out_total = reinterpret_cast<unsigned long long *>(out_total);
+        return launch_k<uint64_t>(h, p, launch_ops, s);
+    }
+}
+
+// Reads the exact size and the sticky device error (synchronizes).
+int read_state(gheap_t h, uint64_t *size_out)
+{
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GHEAP_ERR_CUDA;
+    gh::Hdr hd;
+    if (cudaMemcpy(&hd, h->d_hdr, sizeof(hd), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    int rc = map_dev_err(hd.err);
+    if (rc != GHEAP_OK) h->sticky = rc;
+    uint64_t size = (uint64_t)hd.m * h->k + hd.s;
+    h->size_upper = size;
+    if (size_out) *size_out = size;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *heap_strerror(int code)
+{
+    switch (code) {
+    case GHEAP_OK: return "ok";
+    case GHEAP_ERR_ARG: return "invalid argument";
+    case GHEAP_ERR_OOM: return "device allocation failed";
+    case GHEAP_ERR_FULL: return "heap capacity exceeded";
+    case GHEAP_ERR_TIMEOUT: return "a bounded lock wait gave up";
+    case GHEAP_ERR_CUDA: return "CUDA runtime error";
+    case GHEAP_ERR_STATE: return "impossible node state observed on the device";
+    default: return "unknown error";
+    }
+}
+
+uint64_t heap_slot_to_node(uint64_t j)
+{
+    if (j == 0) return 0;
+    uint32_t d = 63u - (uint32_t)__builtin_clzll(j);
+    if (d == 0) return j;
+    uint64_t o = j - (1ull << d), r = 0;
+    for (uint32_t i = 0; i < d; i++) {
+        r = (r << 1) | (o & 1ull);
+        o >>= 1;
+    }
+    return (1ull << d) + r;
+}
+
+int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k, uint32_t key_bytes,
+                uint32_t flags, uint64_t log_capacity)
+{
+    if (!out) return GHEAP_ERR_ARG;
+    *out = nullptr;
+    if (k < 1 || k > 2048 || (k & (k - 1)) != 0) return GHEAP_ERR_ARG;
+    if (key_bytes != 4 && key_bytes != 8) return GHEAP_ERR_ARG;
+    if (capacity_keys == 0) return GHEAP_ERR_ARG;
+    uint64_t nodes = capacity_keys / k + 1;
+    if (nodes >= (1ull << 30)) return GHEAP_ERR_ARG;
+
+    gheap_t h = (gheap_t)calloc(1, sizeof(gheap_s));
+    if (!h) return GHEAP_ERR_OOM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { free(h); return GHEAP_ERR_CUDA; }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) { free(h); return GHEAP_ERR_CUDA; }
+    h->sm_count = prop.multiProcessorCount;
+    h->k = k;
+    h->key_bytes = key_bytes;
+    h->flags = flags;
+    h->capacity = capacity_keys;
+    h->max_nodes = (uint32_t)nodes;
+    h->ctas = 0;
+    h->ipt = k >= 2048 ? 8 : 4;
+    h->timeout_ns = 2000000000ull;
+    h->log_cap = log_capacity;
+
+    size_t key_bytes_total = ((size_t)h->max_nodes + 1) * k * key_bytes;
+    bool ok = cudaMalloc(&h->d_keys, key_bytes_total) == cudaSuccess &&
+              cudaMalloc((void **)&h->d_state, ((size_t)h->max_nodes + 1) * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&h->d_buf, (size_t)k * key_bytes) == cudaSuccess &&
+              cudaMalloc((void **)&h->d_hdr, sizeof(gh::Hdr)) == cudaSuccess &&
+              cudaMalloc((void **)&h->d_ctl, sizeof(gh::Ctl)) == cudaSuccess &&
+              cudaMalloc((void **)&h->d_stats, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
+    if (ok && log_capacity)
+        ok = cudaMalloc((void **)&h->d_log, log_capacity * sizeof(gheap_log_entry)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        heap_destroy(h);
+        return GHEAP_ERR_OOM;
+    }
+    int rc = heap_reset(h, nullptr);
+    if (rc == GHEAP_OK && cudaDeviceSynchronize() != cudaSuccess) rc = GHEAP_ERR_CUDA;
+    if (rc != GHEAP_OK) {
+        heap_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return GHEAP_OK;
+}
+
+int heap_destroy(gheap_t h)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->d_keys);
+    cudaFree(h->d_state);
+    cudaFree(h->d_buf);
+    cudaFree(h->d_hdr);
+    cudaFree(h->d_ctl);
+    cudaFree(h->d_log);
+    cudaFree(h->d_stats);
+    free(h);
+    return GHEAP_OK;
+}
+
+int heap_reset(gheap_t h, void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    cudaError_t e = cudaMemsetAsync(h->d_state, 0, ((size_t)h->max_nodes + 1) * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hdr, 0, sizeof(gh::Hdr), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, gh::N_STATS * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    h->sticky = GHEAP_OK;
+    h->size_upper = 0;
+    return GHEAP_OK;
+}
+
+int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (items_per_thread != 2 && items_per_thread != 4 && items_per_thread != 8) return GHEAP_ERR_ARG;
+    if (threads_for(h->k, items_per_thread) > 512) return GHEAP_ERR_ARG;
+    h->ctas = ctas;
+    h->ipt = items_per_thread;
+    return GHEAP_OK;
+}
+
+int heap_set_timeout(gheap_t h, uint64_t ns)
+{
+    if (!h || ns == 0) return GHEAP_ERR_ARG;
+    h->timeout_ns = ns;
+    return GHEAP_OK;
+}
+
+int heap_insert(gheap_t h, const void *d_keys, uint64_t n, void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (n == 0) return GHEAP_OK;
+    if (!d_keys) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (h->size_upper + n > h->capacity) {
+        uint64_t size = 0;
+        int rc = read_state(h, &size);
+        if (rc != GHEAP_OK) return rc;
+        if (size + n > h->capacity) return GHEAP_ERR_FULL;
+    }
+    h->size_upper += n;
+    return launch(h, gh::MODE_INSERT, d_keys, nullptr, n, nullptr, 0, nullptr, nullptr,
+                  (cudaStream_t)stream);
+}
+
+int heap_delete_min(gheap_t h, void *d_out, uint64_t n, uint64_t *d_count, void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (n == 0) {
+        if (d_count)
+            return cuda_err(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), (cudaStream_t)stream));
+        return GHEAP_OK;
+    }
+    if (!d_out) return GHEAP_ERR_ARG;
+    if (d_count) {
+        cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), (cudaStream_t)stream);
+        if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    }
+    return launch(h, gh::MODE_DELETE, nullptr, d_out, n, nullptr, 0, nullptr, d_count,
+                  (cudaStream_t)stream);
+}
+
+int heap_ops(gheap_t h, const gheap_op *d_ops, uint64_t n_ops, const void *d_in_keys,
+             void *d_out_keys, uint32_t *d_out_counts, uint64_t max_insert_keys, void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (n_ops == 0) return GHEAP_OK;
+    if (!d_ops) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (h->size_upper + max_insert_keys > h->capacity) {
+        uint64_t size = 0;
+        int rc = read_state(h, &size);
+        if (rc != GHEAP_OK) return rc;
+        if (size + max_insert_keys > h->capacity) return GHEAP_ERR_FULL;
+    }
+    h->size_upper += max_insert_keys;
+    return launch(h, gh::MODE_OPS, d_in_keys, d_out_keys, 0, d_ops, n_ops, d_out_counts, nullptr,
+                  (cudaStream_t)stream);
+}
+
+int heap_sync(gheap_t h)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    return read_state(h, nullptr);
+}
+
+int heap_size(gheap_t h, uint64_t *out)
+{
+    if (!h || !out) return GHEAP_ERR_ARG;
+    return read_state(h, out);
+}
+
+int heap_get_log(gheap_t h, gheap_log_entry *host_buf, uint64_t cap, uint64_t *n_copied,
+                 uint64_t *n_total)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    int rc = read_state(h, nullptr);
+    gh::Hdr hd;
+    if (cudaMemcpy(&hd, h->d_hdr, sizeof(hd), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    uint64_t total = hd.seq;
+    uint64_t avail = total < h->log_cap ? total : h->log_cap;
+    uint64_t n = avail < cap ? avail : cap;
+    if (n && host_buf) {
+        if (cudaMemcpy(host_buf, h->d_log, n * sizeof(gheap_log_entry), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return GHEAP_ERR_CUDA;
+    }
+    if (n_copied) *n_copied = host_buf ? n : 0;
+    if (n_total) *n_total = total;
+    return rc;
+}
+
+int heap_snapshot(gheap_t h, void *host_keys, uint32_t *host_state, void *host_buf,
+                  uint64_t *hdr)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    int rc = read_state(h, nullptr);
+    gh::Hdr hd;
+    if (cudaMemcpy(&hd, h->d_hdr, sizeof(hd), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    size_t slots = (size_t)h->max_nodes + 1;
+    if (host_keys &&
+        cudaMemcpy(host_keys, h->d_keys, slots * h->k * h->key_bytes, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    if (host_state &&
+        cudaMemcpy(host_state, h->d_state, slots * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    if (host_buf &&
+        cudaMemcpy(host_buf, h->d_buf, (size_t)h->k * h->key_bytes, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    if (hdr) {
+        hdr[0] = hd.m;
+        hdr[1] = hd.s;
+        hdr[2] = hd.seq;
+    }
+    return rc;
+}
+
+int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k, uint32_t *key_bytes)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (max_nodes) *max_nodes = h->max_nodes;
+    if (k) *k = h->k;
+    if (key_bytes) *key_bytes = h->key_bytes;
+    return GHEAP_OK;
+}
+
+int heap_debug_hold_root(gheap_t h, void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    // any nonzero word is "held"
+    return cuda_err(cudaMemsetAsync(&h->d_hdr->root_lock, 0x01, sizeof(uint32_t),
+                                    (cudaStream_t)stream));
+}
+
+int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n)
+{
+    if (!h || !out || n > gh::N_STATS) return GHEAP_ERR_ARG;
+    int rc = read_state(h, nullptr);
+    unsigned long long tmp[gh::N_STATS];
+    if (cudaMemcpy(tmp, h->d_stats, sizeof(tmp), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    for (uint32_t i = 0; i < n; i++) out[i] = tmp[i];
+    return rc;
+}
+
+}  // extern "C"

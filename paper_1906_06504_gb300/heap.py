@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in include/gheap.h (argument marshalling only).
+
+Every heap operation runs in the CUDA kernels of libgheap.so; this module
+converts torch tensors to device pointers and streams, and error codes to
+exceptions.  There is no CPU fallback: without the built library or a CUDA
+device the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -5, -6
+FLAG_STATS = 1
+OP_INS, OP_DEL = 1, 2
+
+# gheap_op and gheap_log_entry of include/gheap.h
+OP_DTYPE = np.dtype([("kind", "<u4"), ("n", "<u4"), ("offset", "<u8")])
+LOG_DTYPE = np.dtype([("call_id", "<u4"), ("kind_n", "<u4"), ("ref", "<u8")])
+STAT_NAMES = ("node_loads", "node_stores", "merges", "merges_skipped", "ins_ops",
+              "del_ops", "lock_waits", "root_hold_ns")
+
+_lib = None
+
+
+class GHeapError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = lib().heap_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+
+
+def lib():
+    """Loads libgheap.so (built in-tree by build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libgheap.so is not built (run paper_1906_06504_gb300.build.build())")
+        L = ctypes.CDLL(_build.LIB)
+        vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        sig = {
+            "heap_create": (ctypes.c_int, [ctypes.POINTER(vp), u64, u32, u32, u32, u64]),
+            "heap_destroy": (ctypes.c_int, [vp]),
+            "heap_set_launch": (ctypes.c_int, [vp, u32, u32]),
+            "heap_set_timeout": (ctypes.c_int, [vp, u64]),
+            "heap_insert": (ctypes.c_int, [vp, vp, u64, vp]),
+            "heap_delete_min": (ctypes.c_int, [vp, vp, u64, vp, vp]),
+            "heap_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, u64, vp]),
+            "heap_sync": (ctypes.c_int, [vp]),
+            "heap_size": (ctypes.c_int, [vp, u64p]),
+            "heap_reset": (ctypes.c_int, [vp, vp]),
+            "heap_get_log": (ctypes.c_int, [vp, vp, u64, u64p, u64p]),
+            "heap_snapshot": (ctypes.c_int, [vp, vp, u32p, vp, u64p]),
+            "heap_geometry": (ctypes.c_int, [vp, u64p, u32p, u32p]),
+            "heap_slot_to_node": (u64, [u64]),
+            "heap_get_stats": (ctypes.c_int, [vp, u64p, u32]),
+            "heap_debug_hold_root": (ctypes.c_int, [vp, vp]),
+            "heap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise GHeapError(rc, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def slot_to_node(j):
+    return int(lib().heap_slot_to_node(int(j)))
+
+
+class GHeap:
+    """A generalized concurrent heap in device memory (include/gheap.h)."""
+
+    def __init__(self, capacity, k=1024, key_bytes=4, log_capacity=0, stats=False):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.heap_create(ctypes.byref(h), int(capacity), int(k), int(key_bytes),
+                             FLAG_STATS if stats else 0, int(log_capacity)), "heap_create")
+        self._h = h
+        self.k = int(k)
+        self.key_bytes = int(key_bytes)
+        self.capacity = int(capacity)
+        mn = ctypes.c_uint64()
+        _check(L.heap_geometry(h, ctypes.byref(mn), None, None), "heap_geometry")
+        self.max_nodes = int(mn.value)
+
+    # -- configuration
+    def set_launch(self, ctas=0, items_per_thread=4):
+        _check(lib().heap_set_launch(self._h, int(ctas), int(items_per_thread)), "heap_set_launch")
+
+    def set_timeout(self, ns):
+        _check(lib().heap_set_timeout(self._h, int(ns)), "heap_set_timeout")
+
+    def _key_tensor(self, t, what):
+        if not t.is_cuda:
+            raise ValueError("%s must be a CUDA tensor" % what)
+        if t.element_size() != self.key_bytes:
+            raise ValueError("%s has %d-byte elements, heap keys are %d bytes"
+                             % (what, t.element_size(), self.key_bytes))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+
+    # -- operations
+    def insert(self, keys, stream=None):
+        self._key_tensor(keys, "keys")
+        _check(lib().heap_insert(self._h, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
+                                 _stream_ptr(stream)), "heap_insert")
+
+    def delete_min(self, n, out=None, count=None, stream=None):
+        """Deletes up to n smallest keys into `out` (allocated if None).
+
+        Returns (out, count) with count a 1-element int64 CUDA tensor.
+        """
+        import torch
+        if out is None:
+            dt = torch.int32 if self.key_bytes == 4 else torch.int64
+            out = torch.empty(int(n), dtype=dt, device="cuda")
+        self._key_tensor(out, "out")
+        if out.numel() < n:
+            raise ValueError("out holds %d keys < n=%d" % (out.numel(), n))
+        if count is None:
+            count = torch.empty(1, dtype=torch.int64, device="cuda")
+        _check(lib().heap_delete_min(self._h, ctypes.c_void_p(out.data_ptr()), int(n),
+                                     ctypes.c_void_p(count.data_ptr()), _stream_ptr(stream)),
+               "heap_delete_min")
+        return out, count
+
+    def ops(self, ops_dev, in_keys, out_keys, counts=None, max_insert_keys=None, stream=None):
+        """Runs a device array of gheap_op (viewed as a uint8/int64 tensor)."""
+        n_ops = ops_dev.numel() * ops_dev.element_size() // OP_DTYPE.itemsize
+        if in_keys is not None:
+            self._key_tensor(in_keys, "in_keys")
+        if out_keys is not None:
+            self._key_tensor(out_keys, "out_keys")
+        if max_insert_keys is None:
+            max_insert_keys = in_keys.numel() if in_keys is not None else 0
+        _check(lib().heap_ops(self._h, ctypes.c_void_p(ops_dev.data_ptr()), n_ops,
+                              ctypes.c_void_p(in_keys.data_ptr() if in_keys is not None else 0),
+                              ctypes.c_void_p(out_keys.data_ptr() if out_keys is not None else 0),
+                              ctypes.c_void_p(counts.data_ptr() if counts is not None else 0),
+                              int(max_insert_keys), _stream_ptr(stream)), "heap_ops")
+
+    def sync(self):
+        _check(lib().heap_sync(self._h), "heap_sync")
+
+    def sync_code(self):
+        return int(lib().heap_sync(self._h))
+
+    def size(self):
+        v = ctypes.c_uint64()
+        _check(lib().heap_size(self._h, ctypes.byref(v)), "heap_size")
+        return int(v.value)
+
+    def reset(self, stream=None):
+        _check(lib().heap_reset(self._h, _stream_ptr(stream)), "heap_reset")
+
+    def log(self):
+        """The linearization record as a numpy structured array (LOG_DTYPE)."""
+        L = lib()
+        total = ctypes.c_uint64()
+        got = ctypes.c_uint64()
+        _check(L.heap_get_log(self._h, None, 0, ctypes.byref(got), ctypes.byref(total)),
+               "heap_get_log")
+        buf = np.zeros(int(total.value), dtype=LOG_DTYPE)
+        if total.value:
+            _check(L.heap_get_log(self._h, ctypes.c_void_p(buf.ctypes.data), buf.size,
+                                  ctypes.byref(got), ctypes.byref(total)), "heap_get_log")
+        return buf[:int(got.value)], int(total.value)
+
+    def snapshot(self):
+        """(keys[slots, k], state[slots], buffer[k], (m, s, seq))."""
+        dt = np.uint32 if self.key_bytes == 4 else np.uint64
+        slots = self.max_nodes + 1
+        keys = np.zeros((slots, self.k), dtype=dt)
+        st = np.zeros(slots, dtype=np.uint32)
+        buf = np.zeros(self.k, dtype=dt)
+        hdr = (ctypes.c_uint64 * 3)()
+        _check(lib().heap_snapshot(self._h, ctypes.c_void_p(keys.ctypes.data),
+                                   st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                   ctypes.c_void_p(buf.ctypes.data), hdr), "heap_snapshot")
+        return keys, st, buf, (int(hdr[0]), int(hdr[1]), int(hdr[2]))
+
+    def stats(self):
+        out = (ctypes.c_uint64 * 8)()
+        _check(lib().heap_get_stats(self._h, out, 8), "heap_get_stats")
+        return dict(zip(STAT_NAMES, [int(x) for x in out]))
+
+    def debug_hold_root(self, stream=None):
+        _check(lib().heap_debug_hold_root(self._h, _stream_ptr(stream)), "heap_debug_hold_root")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().heap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
