@@ -385,10 +385,13 @@ int heap_snapshot(gheap_t h, void *host_keys, uint32_t *host_state, void *host_b
         cudaMemcpy(host_keys, h->d_keys, slots * h->k * h->key_bytes, cudaMemcpyDeviceToHost) !=
             cudaSuccess)
         return GHEAP_ERR_CUDA;
-    if (host_state &&
-        cudaMemcpy(host_state, h->d_state, slots * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+    if (host_state) {
+        if (cudaMemcpy(host_state, h->d_state, slots * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
             cudaSuccess)
-        return GHEAP_ERR_CUDA;
+            return GHEAP_ERR_CUDA;
+        // the root is guarded by the header's root lock, not by a state word
+        host_state[1] = hd.m >= 1 ? gh::ST_AVAIL : gh::ST_EMPTY;
+    }
     if (host_buf &&
         cudaMemcpy(host_buf, h->d_buf, (size_t)h->k * h->key_bytes, cudaMemcpyDeviceToHost) !=
             cudaSuccess)
