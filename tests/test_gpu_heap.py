@@ -135,18 +135,28 @@ def test_concurrent_phased(dist):
         h.sync()
         check_properties(h)
         assert h.size() == n
-        st = h.stats()
-        if dist == "ascending":
-            # ascending input: every insert finds the keys already on its
-            # path below its own and never merges (Section 5.2); only the
-            # final partial batch merges with the root
-            assert st["merges"] <= 1, st
         rec = r.delete_min(n)
         h.sync()
         out = to_host(rec["out"], 4)
         assert int(rec["cnt"].item()) == n
         assert np.array_equal(out, np.sort(keys))
         r.replay_and_compare()
+
+
+def test_ascending_input_never_merges():
+    """Ascending keys, one block: every insert finds smaller keys on its whole
+    path and only places its batch at the target, with no MergeAndSort
+    (Section 5.2); deleteMin-all still returns the input."""
+    n, k = 1 << 14, 64
+    keys = inputs.keys_u32(inputs.config_seed(1), n, "ascending")
+    with GHeap(capacity=n, k=k, stats=True) as h:
+        h.set_launch(ctas=1)
+        h.insert(to_dev(keys))
+        st = h.stats()
+        assert st["merges"] == 0 and st["ins_ops"] == n // k, st
+        out, cnt = h.delete_min(n)
+        h.sync()
+        assert np.array_equal(to_host(out, 4), keys)
 
 
 @pytest.mark.parametrize("k,key_bytes,partial", [(1024, 4, False), (1024, 4, True),
