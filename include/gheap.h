@@ -85,7 +85,7 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k,
 int heap_destroy(gheap_t h);
 
 /* Launch shape of the persistent kernels: `ctas` thread blocks (0 = as many
- * as fit on the device at once) of 2k/items_per_thread threads (at least 32,
+ * as fit on the device at once) of 2k/items_per_thread threads (at least 64,
  * at most 512), items_per_thread in {2, 4, 8}.  The paper's best setting is
  * k = 1024 with 512 threads (Section 5.4), i.e. items_per_thread = 4, the
  * default. */
@@ -153,10 +153,15 @@ int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k,
  * (Section 4.3).  The map is its own inverse. */
 uint64_t heap_slot_to_node(uint64_t j);
 
-/* Device counters when created with GHEAP_FLAG_STATS (synchronizes):
+/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 20:
  * out[0] node loads, out[1] node stores, out[2] merges, out[3] merges skipped
  * as disjoint (Section 4.3), out[4] INS ops, out[5] DEL ops, out[6] lock
- * waits that spun, out[7] sum of root-hold time in ns.  n <= 8. */
+ * waits that spun, out[7] sum of root-hold time in ns; then SM cycles seen
+ * by the operating block per phase: DEL root-lock wait [8], DEL root step
+ * before the children [9], DEL child-lock waits [10], child loads [11],
+ * merges [12], stores + releases [13], DEL sift levels [14], INS root-lock
+ * wait [15], INS batch sort [16], INS node-lock waits [17], INS level steps
+ * [18], INS levels [19]. */
 int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
 
 /* Test hook for the bounded waits: marks the root lock as held, with no

@@ -49,10 +49,12 @@ int map_dev_err(uint32_t e)
     }
 }
 
+// Threads per block: 2k/ipt merge outputs per thread, and at least two warps
+// (thread 0 and thread 32 take node locks in parallel).
 uint32_t threads_for(uint32_t k, uint32_t ipt)
 {
     uint32_t t = 2 * k / ipt;
-    if (t < 32) t = 32;
+    if (t < 64) t = 64;
     return t;
 }
 
@@ -148,7 +150,7 @@ int read_state(gheap_t h, uint64_t *size_out)
         return GHEAP_ERR_CUDA;
     int rc = map_dev_err(hd.err);
     if (rc != GHEAP_OK) h->sticky = rc;
-    uint64_t size = (uint64_t)hd.m * h->k + hd.s;
+    uint64_t size = (uint64_t)gh::rw_m(hd.root) * h->k + gh::rw_s(hd.root);
     h->size_upper = size;
     if (size_out) *size_out = size;
     return rc;
@@ -390,15 +392,15 @@ int heap_snapshot(gheap_t h, void *host_keys, uint32_t *host_state, void *host_b
             cudaSuccess)
             return GHEAP_ERR_CUDA;
         // the root is guarded by the header's root lock, not by a state word
-        host_state[1] = hd.m >= 1 ? gh::ST_AVAIL : gh::ST_EMPTY;
+        host_state[1] = gh::rw_m(hd.root) >= 1 ? gh::ST_AVAIL : gh::ST_EMPTY;
     }
     if (host_buf &&
         cudaMemcpy(host_buf, h->d_buf, (size_t)h->k * h->key_bytes, cudaMemcpyDeviceToHost) !=
             cudaSuccess)
         return GHEAP_ERR_CUDA;
     if (hdr) {
-        hdr[0] = hd.m;
-        hdr[1] = hd.s;
+        hdr[0] = gh::rw_m(hd.root);
+        hdr[1] = gh::rw_s(hd.root);
         hdr[2] = hd.seq;
     }
     return rc;
@@ -417,8 +419,8 @@ int heap_debug_hold_root(gheap_t h, void *stream)
 {
     if (!h) return GHEAP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
-    // any nonzero word is "held"
-    return cuda_err(cudaMemsetAsync(&h->d_hdr->root_lock, 0x01, sizeof(uint32_t),
+    // a nonzero top byte is "held"
+    return cuda_err(cudaMemsetAsync(&h->d_hdr->root, 0x01, sizeof(unsigned long long),
                                     (cudaStream_t)stream));
 }
 

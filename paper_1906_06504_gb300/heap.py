@@ -21,7 +21,10 @@ OP_INS, OP_DEL = 1, 2
 OP_DTYPE = np.dtype([("kind", "<u4"), ("n", "<u4"), ("offset", "<u8")])
 LOG_DTYPE = np.dtype([("call_id", "<u4"), ("kind_n", "<u4"), ("ref", "<u8")])
 STAT_NAMES = ("node_loads", "node_stores", "merges", "merges_skipped", "ins_ops",
-              "del_ops", "lock_waits", "root_hold_ns")
+              "del_ops", "lock_waits", "root_hold_ns",
+              "del_acquire_cyc", "del_root_step_cyc", "del_child_wait_cyc",
+              "del_child_load_cyc", "del_merge_cyc", "del_store_release_cyc", "del_levels",
+              "ins_acquire_cyc", "ins_sort_cyc", "ins_wait_cyc", "ins_step_cyc", "ins_levels")
 
 _lib = None
 
@@ -199,8 +202,8 @@ class GHeap:
         return keys, st, buf, (int(hdr[0]), int(hdr[1]), int(hdr[2]))
 
     def stats(self):
-        out = (ctypes.c_uint64 * 8)()
-        _check(lib().heap_get_stats(self._h, out, 8), "heap_get_stats")
+        out = (ctypes.c_uint64 * len(STAT_NAMES))()
+        _check(lib().heap_get_stats(self._h, out, len(STAT_NAMES)), "heap_get_stats")
         return dict(zip(STAT_NAMES, [int(x) for x in out]))
 
     def debug_hold_root(self, stream=None):
