@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--keys", type=int, default=N_KEYS)
     ap.add_argument("--k", type=int, default=K)
     ap.add_argument("--ctas", type=int, default=0)
-    ap.add_argument("--ipt", type=int, default=4)
+    ap.add_argument("--ipt", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -85,10 +85,12 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k,
 int heap_destroy(gheap_t h);
 
 /* Launch shape of the persistent kernels: `ctas` thread blocks (0 = as many
- * as fit on the device at once) of 2k/items_per_thread threads (at least 64,
- * at most 512), items_per_thread in {2, 4, 8}.  The paper's best setting is
- * k = 1024 with 512 threads (Section 5.4), i.e. items_per_thread = 4, the
- * default. */
+ * as fit on the device at once), each of 2k/items_per_thread merge threads
+ * (at least 32; at most 512 for items_per_thread 4, 256 for 8 and 16) plus
+ * one control warp that takes the node locks; items_per_thread in {4, 8, 16}.
+ * The paper's best setting is k = 1024 with 512 threads (Section 5.4), i.e.
+ * items_per_thread = 4; the default is 8 (256 merge threads and more
+ * registers per thread, measured faster on GB300), 16 for k = 2048. */
 int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread);
 
 /* Bound on every lock wait, in nanoseconds (default 2e9).  A wait that runs

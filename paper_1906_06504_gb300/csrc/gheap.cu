@@ -49,21 +49,26 @@ int map_dev_err(uint32_t e)
     }
 }
 
-// Threads per block: 2k/ipt merge outputs per thread, and at least two warps
-// (thread 0 and thread 32 take node locks in parallel).
-uint32_t threads_for(uint32_t k, uint32_t ipt)
+// Threads per block: the merge threads (2k/ipt merge outputs each, at least
+// one warp, at most 512) plus one control warp.
+uint32_t merge_threads_for(uint32_t k, uint32_t ipt)
 {
     uint32_t t = 2 * k / ipt;
-    if (t < 64) t = 64;
+    if (t < 32) t = 32;
     return t;
 }
+
+uint32_t threads_for(uint32_t k, uint32_t ipt) { return merge_threads_for(k, ipt) + 32; }
+
+// Merge threads allowed by the kernel's launch bound for this merge width.
+uint32_t max_merge_threads(uint32_t ipt) { return ipt >= 8 ? 256 : 512; }
 
 template <typename K, int IPT>
 int launch_t(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
     auto kern = gh::heap_kernel<K, IPT>;
     const uint32_t threads = threads_for(h->k, IPT);
-    const size_t smem = 4u * (size_t)h->k * sizeof(K);
+    const size_t smem = 6u * (size_t)h->k * sizeof(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return GHEAP_ERR_CUDA;
@@ -84,9 +89,9 @@ template <typename K>
 int launch_k(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
     switch (h->ipt) {
-    case 2: return launch_t<K, 2>(h, p, n_ops, s);
     case 4: return launch_t<K, 4>(h, p, n_ops, s);
     case 8: return launch_t<K, 8>(h, p, n_ops, s);
+    case 16: return launch_t<K, 16>(h, p, n_ops, s);
     default: return GHEAP_ERR_ARG;
     }
 }
@@ -96,16 +101,16 @@ gh::Params<K> base_params(gheap_t h, uint32_t mode)
 {
     gh::Params<K> p;
     memset(&p, 0, sizeof(p));
-    p.keys = static_cast<K *>(h->d_keys);
-    p.state = h->d_state;
-    p.buf = static_cast<K *>(h->d_buf);
-    p.hdr = h->d_hdr;
+    p.h.keys = static_cast<K *>(h->d_keys);
+    p.h.state = h->d_state;
+    p.h.buf = static_cast<K *>(h->d_buf);
+    p.h.hdr = h->d_hdr;
+    p.h.log = h->d_log;
+    p.h.log_cap = h->log_cap;
+    p.h.max_nodes = h->max_nodes;
     p.ctl = h->d_ctl;
-    p.log = h->d_log;
-    p.log_cap = h->log_cap;
     p.stats = (h->flags & GHEAP_FLAG_STATS) ? h->d_stats : nullptr;
     p.k = h->k;
-    p.max_nodes = h->max_nodes;
     p.timeout_ns = h->timeout_ns;
     p.mode = mode;
     p.call_id = ++h->call_id;
@@ -210,7 +215,7 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k, uint32_t key_b
     h->capacity = capacity_keys;
     h->max_nodes = (uint32_t)nodes;
     h->ctas = 0;
-    h->ipt = k >= 2048 ? 8 : 4;
+    h->ipt = k >= 2048 ? 16 : 8;
     h->timeout_ns = 2000000000ull;
     h->log_cap = log_capacity;
 
@@ -271,8 +276,10 @@ int heap_reset(gheap_t h, void *stream)
 int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread)
 {
     if (!h) return GHEAP_ERR_ARG;
-    if (items_per_thread != 2 && items_per_thread != 4 && items_per_thread != 8) return GHEAP_ERR_ARG;
-    if (threads_for(h->k, items_per_thread) > 512) return GHEAP_ERR_ARG;
+    if (items_per_thread != 4 && items_per_thread != 8 && items_per_thread != 16)
+        return GHEAP_ERR_ARG;
+    if (merge_threads_for(h->k, items_per_thread) > max_merge_threads(items_per_thread))
+        return GHEAP_ERR_ARG;
     h->ctas = ctas;
     h->ipt = items_per_thread;
     return GHEAP_OK;

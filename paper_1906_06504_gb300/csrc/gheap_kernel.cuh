@@ -13,22 +13,26 @@
 //     MARKED, Section 3.3.2) taken with atomicCAS in parent-before-child
 //     order (Section 3.3.1), and a DEL whose last node is an in-flight INS
 //     target marks it and receives that INS's keys (Section 3.3.2);
-//   * one thread block runs one operation (Section 4); merges use the
-//     merge-path partition (Section 4.2), batch sorting a block bitonic
-//     sort (Section 4.1), and node pairs whose key ranges do not overlap are
-//     kept or swapped without merging (Section 4.3).
+//   * one thread block runs one operation (Section 4); merges are block-wide
+//     (Section 4.2), batch sorting is a block bitonic sort (Section 4.1), and
+//     node pairs whose key ranges do not overlap are kept or swapped without
+//     merging (Section 4.3).
 //
-// GB300 specifics.  The root is the serial point of every operation
-// (Section 3.3.3), so the kernel is built to shorten each lock hold rather
-// than to stream bytes:
+// GB300 organisation.  The root lock is the serial point of every operation
+// (Section 3.3.3) and each level of a walk waits on its predecessor's
+// release, so the kernel is built to shorten lock holds:
+//   * a block is nmt() "merge threads" plus one control warp.  The control
+//     warp takes every lock (an acquire stalls only that warp), issues the
+//     cp.async copies of the nodes it has locked -- for the next level while
+//     the merge threads still work on this one -- and publishes releases
+//     while the merge threads go on.  Merge threads synchronise among
+//     themselves on named barrier 1; the whole block meets on barrier 0 only
+//     where data or lock results change hands;
 //   * the root lock, the node count m and the buffer size s share one 64-bit
 //     word: acquiring the root returns the header, releasing it publishes
-//     the new header;
-//   * node batches move global -> shared with cp.async (16-byte, L2 only),
-//     issued as soon as the node is locked and overlapped with other work;
-//   * the lock of the next node on a path is tried with a single CAS while
-//     the current level's MergeAndSort runs, and the two children of a DEL
-//     are locked by two warps at once;
+//     the new one; the root is released before any deeper prefetch;
+//   * MergeAndSort of two full nodes is a bitonic merge (shared-memory stages
+//     for wide strides, warp shuffles and registers for the rest);
 //   * persistent thread blocks pull operations from a device counter;
 //   * every wait is bounded by %globaltimer and reports a sticky error.
 #pragma once
@@ -49,34 +53,31 @@ enum : uint32_t {
     ST_DELIVERED = 5
 };
 constexpr uint32_t ST_GAVE_UP = ~0u;
+constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
 enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2 };
 
 enum : uint32_t { E_NONE = 0, E_TIMEOUT = 1, E_FULL = 2, E_STATE = 3 };
 
 // Counters kept when the heap is created with GHEAP_FLAG_STATS.  The *_CYC
-// entries are SM cycles seen by thread 0 of the operating block, per phase.
+// entries are SM cycles of one observer thread per phase.
 enum : uint32_t {
     STAT_LOADS = 0, STAT_STORES = 1, STAT_MERGES = 2, STAT_SKIPS = 3,
     STAT_INS = 4, STAT_DEL = 5, STAT_WAITS = 6, STAT_ROOT_NS = 7,
     STAT_DEL_ACQ_CYC = 8,       // waiting for the root lock
-    STAT_DEL_ROOT_CYC = 9,      // root step before the children: loads, last node, refill
-    STAT_DEL_WAIT_CYC = 10,     // waiting for child locks (all levels)
-    STAT_DEL_LOAD_CYC = 11,     // loading children (all levels)
-    STAT_DEL_MERGE_CYC = 12,    // MergeAndSorts (all levels)
-    STAT_DEL_REL_CYC = 13,      // node stores and lock releases (all levels)
+    STAT_DEL_ROOT_CYC = 9,      // root step: loads, last node, children, refill
+    STAT_DEL_WAIT_CYC = 10,     // control warp: child locks and copies
+    STAT_DEL_LOAD_CYC = 11,     // (unused)
+    STAT_DEL_MERGE_CYC = 12,    // merge threads: MergeAndSorts and stores
+    STAT_DEL_REL_CYC = 13,      // control warp: lock releases
     STAT_DEL_LEVELS = 14,       // sift levels visited
     STAT_INS_ACQ_CYC = 15,      // waiting for the root lock
     STAT_INS_SORT_CYC = 16,     // staging and sorting the batch
-    STAT_INS_WAIT_CYC = 17,     // waiting for node locks below the root
-    STAT_INS_STEP_CYC = 18,     // level steps: merge, store, release, next load
+    STAT_INS_WAIT_CYC = 17,     // control warp: node locks and copies
+    STAT_INS_STEP_CYC = 18,     // merge threads: level steps
     STAT_INS_LEVELS = 19,       // levels visited
     N_STATS = 20
 };
-
-// The thread that takes node locks beside thread 0 (lane 0 of warp 1; every
-// launch has at least two warps).
-constexpr uint32_t T2 = 32;
 
 // Root word: bits 0-31 m (full nodes), bits 32-47 s (partial-buffer keys),
 // a nonzero top byte = held.
@@ -111,21 +112,29 @@ struct __align__(16) Ctl {
     uint32_t _pad;
 };
 
+// The device arrays of one heap.
 template <typename K>
-struct Params {
+struct HeapView {
     K *keys;                  // (max_nodes + 1) * k keys, slot j at j*k
     uint32_t *state;          // max_nodes + 1 lock words, by slot
     K *buf;                   // partial buffer, k keys
     Hdr *hdr;
-    Ctl *ctl;
     gheap_log_entry *log;
     unsigned long long log_cap;
+    uint32_t max_nodes;
+    uint32_t _pad;
+};
+
+template <typename K>
+struct Params {
+    HeapView<K> h;
+    Ctl *ctl;
     unsigned long long *stats;   // N_STATS counters or nullptr
     uint32_t k;
-    uint32_t max_nodes;
-    unsigned long long timeout_ns;
     uint32_t mode;
     uint32_t call_id;
+    uint32_t _pad;
+    unsigned long long timeout_ns;
     const K *in;                 // MODE_INSERT / MODE_OPS input keys
     K *out;                      // MODE_DELETE / MODE_OPS output keys
     unsigned long long n;        // MODE_INSERT: keys; MODE_DELETE: keys wanted
@@ -135,19 +144,39 @@ struct Params {
     unsigned long long *out_total;  // MODE_DELETE, may be nullptr
 };
 
-// Block-shared scalars that carry the lock threads' decisions to the block.
+// Block-shared scalars that carry decisions between the control warp and the
+// merge threads (always across a block barrier).
 struct Shared {
     unsigned long long op;
     unsigned long long seq;
     unsigned long long out_off;
     unsigned long long t_root;
-    uint32_t m, s, take;
+    uint32_t m, s, take, tslot;
     int stop;
     int abort;
-    uint32_t lk0, lk1;     // lock results of thread 0 / thread T2
     int deliver;
+    int halt;                 // DEL: the sift ends after MergeAndSort(l, r)
+    uint32_t lk[2][2];        // lock results, double-buffered by level
     unsigned long long cnt[N_STATS];
 };
+
+// ---------------------------------------------------------------------------
+// block roles and barriers
+// ---------------------------------------------------------------------------
+
+// Merge threads are threadIdx.x < nmt(); the last warp is the control warp.
+__device__ __forceinline__ uint32_t nmt() { return blockDim.x - 32u; }
+__device__ __forceinline__ bool is_ctrl() { return threadIdx.x >= blockDim.x - 32u; }
+__device__ __forceinline__ uint32_t clane() { return threadIdx.x - (blockDim.x - 32u); }
+
+// Whole block (named barrier 0).
+__device__ __forceinline__ void bar_all() { __syncthreads(); }
+
+// Merge threads only (named barrier 1).
+__device__ __forceinline__ void bar_mg()
+{
+    asm volatile("bar.sync 1, %0;" :: "r"(blockDim.x - 32u) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // memory-model helpers
@@ -207,27 +236,16 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
-}
-
-// Publishes `v` on lock word `w` for the whole block.  The barrier orders
-// every thread's earlier writes before thread 0's st.release.gpu, and a
-// release is cumulative over the writes its thread has observed, so a block
-// that acquires `w` sees all of them (the same barrier + single release-store
-// hand-off that split-K GEMM epilogues use between thread blocks).
-__device__ __forceinline__ void block_release(uint32_t *w, uint32_t v)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) st_release(w, v);
-}
-
+// Releases (st.release.gpu) are issued by control lane 0 after a block
+// barrier that follows the merge threads' stores: the barrier orders those
+// stores before the release, and a release is cumulative over the writes its
+// thread has observed, so a block that acquires the word sees all of them
+// (the barrier + single release-store hand-off used between thread blocks by
+// split-K GEMM epilogues).
 template <typename K>
-__device__ __forceinline__ void release_root(const Params<K> &p, uint32_t m, uint32_t s)
+__device__ __forceinline__ void release_root_word(const HeapView<K> &H, uint32_t m, uint32_t s)
 {
-    __syncthreads();
-    if (threadIdx.x == 0) st_release64(&p.hdr->root, rw_make(m, s));
+    st_release64(&H.hdr->root, rw_make(m, s));
 }
 
 template <typename K>
@@ -245,37 +263,48 @@ __device__ __forceinline__ uint32_t slot_node(uint32_t j)
     return (1u << d) + (__brev(o) >> (32u - d));
 }
 
+// Children of tree node `node` that exist in storage: slot numbers, or 0.
+__device__ __forceinline__ void child_slots(uint32_t node, uint32_t max_nodes, uint32_t &sl,
+                                            uint32_t &sr)
+{
+    const uint32_t l = 2 * node;
+    sl = sr = 0;
+    if (level_of(l) <= level_of(max_nodes)) {
+        const uint32_t a = slot_node(l), b = slot_node(l + 1);
+        sl = a <= max_nodes ? a : 0;
+        sr = b <= max_nodes ? b : 0;
+    }
+}
+
 __device__ __forceinline__ void stat_add(Shared &sh, uint32_t i, unsigned long long v)
 {
     atomicAdd(&sh.cnt[i], v);
 }
 
-// Phase timer of thread 0: adds the cycles since `t` to counter i, restarts.
+// Phase timer of one observer thread: adds the cycles since `t`, restarts.
 __device__ __forceinline__ void lap(Shared &sh, uint32_t i, long long &t)
 {
-    if (threadIdx.x == 0) {
-        const long long now = clock64();
-        atomicAdd(&sh.cnt[i], (unsigned long long)(now - t));
-        t = now;
-    }
+    const long long now = clock64();
+    atomicAdd(&sh.cnt[i], (unsigned long long)(now - t));
+    t = now;
 }
 
 // ---------------------------------------------------------------------------
-// bounded waits (single thread)
+// bounded waits (single control lane)
 // ---------------------------------------------------------------------------
 
 template <typename K>
-__device__ __forceinline__ bool keep_waiting(const Params<K> &p, unsigned long long &t0,
-                                             uint32_t &it)
+__device__ __forceinline__ bool keep_waiting(const Params<K> &p, const HeapView<K> &H,
+                                             unsigned long long &t0, uint32_t &it)
 {
     ++it;
     if ((it & 7u) == 0) {
-        if (ld_relaxed(&p.hdr->err) != E_NONE) return false;
+        if (ld_relaxed(&H.hdr->err) != E_NONE) return false;
         unsigned long long now = gtimer();
         if (t0 == 0) {
             t0 = now;
         } else if (now - t0 > p.timeout_ns) {
-            atomicCAS(&p.hdr->err, E_NONE, E_TIMEOUT);
+            atomicCAS(&H.hdr->err, E_NONE, E_TIMEOUT);
             return false;
         }
     }
@@ -284,17 +313,18 @@ __device__ __forceinline__ bool keep_waiting(const Params<K> &p, unsigned long l
 }
 
 template <typename K>
-__device__ __forceinline__ void set_err(const Params<K> &p, uint32_t e)
+__device__ __forceinline__ void set_err(const HeapView<K> &H, uint32_t e)
 {
-    atomicCAS(&p.hdr->err, E_NONE, e);
+    atomicCAS(&H.hdr->err, E_NONE, e);
 }
 
 // Root lock (also guards the partial buffer and the header).  Returns false
 // when the wait gave up; `word` receives the header (m, s).
 template <typename K>
-__device__ bool lock_root(const Params<K> &p, Shared &sh, unsigned long long &word)
+__device__ bool lock_root(const Params<K> &p, const HeapView<K> &H, Shared &sh,
+                          unsigned long long &word)
 {
-    unsigned long long *w = &p.hdr->root;
+    unsigned long long *w = &H.hdr->root;
     unsigned long long t0 = 0;
     uint32_t it = 0;
     for (;;) {
@@ -307,7 +337,7 @@ __device__ bool lock_root(const Params<K> &p, Shared &sh, unsigned long long &wo
                 return true;
             }
         }
-        if (!keep_waiting(p, t0, it)) return false;
+        if (!keep_waiting(p, H, t0, it)) return false;
     }
 }
 
@@ -323,7 +353,8 @@ __device__ __forceinline__ uint32_t try_lock(uint32_t *w)
 // state when the slot holds no lockable node (EMPTY, TARGET, MARKED,
 // DELIVERED), or ST_GAVE_UP.
 template <typename K>
-__device__ uint32_t lock_node(const Params<K> &p, Shared &sh, uint32_t *w, uint32_t first)
+__device__ uint32_t lock_node(const Params<K> &p, const HeapView<K> &H, Shared &sh,
+                              uint32_t *w, uint32_t first)
 {
     uint32_t v = first;
     if (v != ST_INUSE) return v;
@@ -331,7 +362,7 @@ __device__ uint32_t lock_node(const Params<K> &p, Shared &sh, uint32_t *w, uint3
     uint32_t it = 0;
     stat_add(sh, STAT_WAITS, 1);
     for (;;) {
-        if (!keep_waiting(p, t0, it)) return ST_GAVE_UP;
+        if (!keep_waiting(p, H, t0, it)) return ST_GAVE_UP;
         v = ld_relaxed(w);
         if (v == ST_AVAIL) v = try_lock(w);
         if (v != ST_INUSE) return v;
@@ -348,9 +379,10 @@ __device__ __forceinline__ uint32_t claim_target(uint32_t *w)
 // DEL takes the last node, `first` being an earlier try: lock it if it is a
 // stored node; if it is the target of an INS still in flight, mark it and wait
 // until that INS delivers its keys there (Section 3.3.2, INS/DEL cooperation).
-// The caller holds the root and no other lock.
+// While it waits for a delivery the caller holds the root and no node lock.
 template <typename K>
-__device__ bool take_last(const Params<K> &p, Shared &sh, uint32_t *w, uint32_t first)
+__device__ bool take_last(const Params<K> &p, const HeapView<K> &H, Shared &sh, uint32_t *w,
+                          uint32_t first)
 {
     unsigned long long t0 = 0;
     uint32_t it = 0;
@@ -368,17 +400,17 @@ __device__ bool take_last(const Params<K> &p, Shared &sh, uint32_t *w, uint32_t 
                         return true;
                     }
                     if (v != ST_MARKED) {
-                        set_err(p, E_STATE);
+                        set_err(H, E_STATE);
                         return false;
                     }
-                    if (!keep_waiting(p, t0, it)) return false;
+                    if (!keep_waiting(p, H, t0, it)) return false;
                 }
             }
         } else if (v != ST_INUSE) {
-            set_err(p, E_STATE);
+            set_err(H, E_STATE);
             return false;
         }
-        if (!keep_waiting(p, t0, it)) return false;
+        if (!keep_waiting(p, H, t0, it)) return false;
         v = ld_relaxed(w);
         if (v == ST_AVAIL) {
             v = try_lock(w);
@@ -388,7 +420,7 @@ __device__ bool take_last(const Params<K> &p, Shared &sh, uint32_t *w, uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// block-wide data movement
+// data movement
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -397,54 +429,57 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(gmem) : "memory");
 }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// Waits for this thread's async copies, then for the block.
-__device__ __forceinline__ void cp_async_join()
+__device__ __forceinline__ void cp_async_commit()
 {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// global (L2) -> shared, asynchronous when aligned (complete with
-// cp_async_join); small or unaligned batches are copied synchronously.
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// global (L2) -> shared by `nthr` threads with index `t`; cp.async when
+// aligned (complete with cp_async_wait and a barrier), else synchronous.
 template <typename K>
-__device__ __forceinline__ void g2s_async(K *dst, const K *src, uint32_t n)
+__device__ __forceinline__ void g2s(K *dst, const K *src, uint32_t n, uint32_t t, uint32_t nthr)
 {
     const uint32_t bytes = n * (uint32_t)sizeof(K);
     if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 &&
         (bytes & 15u) == 0) {
         const char *s = reinterpret_cast<const char *>(src);
         char *d = reinterpret_cast<char *>(dst);
-        for (uint32_t i = threadIdx.x; i < bytes / 16u; i += blockDim.x)
-            cp_async16(d + 16u * i, s + 16u * i);
+        for (uint32_t i = t; i < bytes / 16u; i += nthr) cp_async16(d + 16u * i, s + 16u * i);
     } else {
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldcg(src + i);
+        for (uint32_t i = t; i < n; i += nthr) dst[i] = __ldcg(src + i);
     }
 }
 
-// shared -> global (L2)
+// shared -> global (L2) by the merge threads.
 template <typename K>
 __device__ __forceinline__ void s2g(K *dst, const K *src, uint32_t n)
 {
+    const uint32_t t = threadIdx.x, nthr = nmt();
     const uint32_t bytes = n * (uint32_t)sizeof(K);
     if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 &&
         (bytes & 15u) == 0) {
         const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
         uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-        for (uint32_t i = threadIdx.x; i < bytes / 16u; i += blockDim.x) __stcg(d4 + i, s4[i]);
+        for (uint32_t i = t; i < bytes / 16u; i += nthr) __stcg(d4 + i, s4[i]);
     } else {
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) __stcg(dst + i, src[i]);
+        for (uint32_t i = t; i < n; i += nthr) __stcg(dst + i, src[i]);
     }
 }
 
-// Block bitonic sort of a[0..k), k a power of two, ascending (Section 4.1).
+// Block bitonic sort of a[0..k) by the merge threads, k a power of two,
+// ascending (Section 4.1).
 template <typename K>
-__device__ void block_sort(K *a, uint32_t k)
+__device__ __noinline__ void block_sort(K *a, uint32_t k)
 {
+    const uint32_t T = nmt();
     for (uint32_t size = 2; size <= k; size <<= 1) {
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < (k >> 1); i += blockDim.x) {
+            for (uint32_t i = threadIdx.x; i < (k >> 1); i += T) {
                 uint32_t lo = 2 * i - (i & (stride - 1));
                 uint32_t hi = lo + stride;
                 bool asc = (lo & size) == 0;
@@ -454,19 +489,19 @@ __device__ void block_sort(K *a, uint32_t k)
                     a[hi] = x;
                 }
             }
-            __syncthreads();
+            bar_mg();
         }
     }
 }
 
 // MergeAndSort of two ascending runs in shared memory (Section 3.2.1) by the
-// merge-path partition (Section 4.2): output position q < split goes to
-// dlo[q], the rest to dhi[q - split].  Thread t produces outputs
-// [t*IPT, t*IPT + IPT); na + nb must not exceed IPT * blockDim.x.  The
-// destinations may alias the sources.  Ends with a barrier.
+// merge-path partition (Section 4.2), merge threads only: output position
+// q < split goes to dlo[q], the rest to dhi[q - split].  Thread t produces
+// outputs [t*IPT, t*IPT + IPT); na + nb must not exceed IPT * nmt().  The
+// destinations may alias the sources.  Ends with bar_mg.
 template <typename K, int IPT>
-__device__ __forceinline__ void merge_split(const K *a, uint32_t na, const K *b, uint32_t nb,
-                                            K *dlo, uint32_t split, K *dhi)
+__device__ __noinline__ void merge_split(const K *a, uint32_t na, const K *b, uint32_t nb,
+                                         K *dlo, uint32_t split, K *dhi)
 {
     const uint32_t total = na + nb;
     const uint32_t start = threadIdx.x * IPT;
@@ -498,7 +533,7 @@ __device__ __forceinline__ void merge_split(const K *a, uint32_t na, const K *b,
             }
         }
     }
-    __syncthreads();
+    bar_mg();
     if (start < total) {
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
@@ -509,7 +544,59 @@ __device__ __forceinline__ void merge_split(const K *a, uint32_t na, const K *b,
             }
         }
     }
-    __syncthreads();
+    bar_mg();
+}
+
+// N contiguous keys between shared memory and registers with the widest
+// aligned vector accesses (16 or 8 bytes), so that a warp touching
+// consecutive runs stays free of bank conflicts.  `p` must be aligned to the
+// run's size when that is 8 or 16 bytes or a multiple of 16.
+template <typename K, int N>
+__device__ __forceinline__ void ld_run(const K *p, K (&v)[N])
+{
+    constexpr int B = (int)sizeof(K) * N;
+    if constexpr (B % 16 == 0) {
+        constexpr int PER = 16 / (int)sizeof(K);
+#pragma unroll
+        for (int c = 0; c < N / PER; ++c) {
+            union { uint4 u; K k[PER]; } t;
+            t.u = reinterpret_cast<const uint4 *>(p)[c];
+#pragma unroll
+            for (int e = 0; e < PER; ++e) v[c * PER + e] = t.k[e];
+        }
+    } else if constexpr (B == 8) {
+        union { uint2 u; K k[N]; } t;
+        t.u = *reinterpret_cast<const uint2 *>(p);
+#pragma unroll
+        for (int e = 0; e < N; ++e) v[e] = t.k[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) v[e] = p[e];
+    }
+}
+
+template <typename K, int N>
+__device__ __forceinline__ void st_run(K *p, const K (&v)[N])
+{
+    constexpr int B = (int)sizeof(K) * N;
+    if constexpr (B % 16 == 0) {
+        constexpr int PER = 16 / (int)sizeof(K);
+#pragma unroll
+        for (int c = 0; c < N / PER; ++c) {
+            union { uint4 u; K k[PER]; } t;
+#pragma unroll
+            for (int e = 0; e < PER; ++e) t.k[e] = v[c * PER + e];
+            reinterpret_cast<uint4 *>(p)[c] = t.u;
+        }
+    } else if constexpr (B == 8) {
+        union { uint2 u; K k[N]; } t;
+#pragma unroll
+        for (int e = 0; e < N; ++e) t.k[e] = v[e];
+        *reinterpret_cast<uint2 *>(p) = t.u;
+    } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) p[e] = v[e];
+    }
 }
 
 // MergeAndSort of two full ascending runs a[0..k), b[0..k) (Section 3.2.1) as
@@ -517,47 +604,56 @@ __device__ __forceinline__ void merge_split(const K *a, uint32_t na, const K *b,
 // across the halves leaves the k smallest in dlo and the k largest in dhi,
 // each a bitonic run; each half is then sorted by its own half-cleaner
 // stages -- strides of 32*IPT keys and more in shared memory, smaller ones
-// in registers via warp shuffles.  Needs blockDim.x * IPT == 2k and k >=
-// 32 * IPT; destinations may alias the sources.  Ends with a barrier.
+// in registers via warp shuffles.  Every thread moves contiguous runs of
+// IPT/2 or IPT keys with vector accesses.  Merge threads only; needs
+// nmt()*IPT == 2k and k >= 32*IPT; destinations may alias the sources.  Ends
+// with bar_mg.
 template <typename K, int IPT>
-__device__ __forceinline__ void merge_full(const K *a, const K *b, K *dlo, K *dhi, uint32_t k)
+__device__ __noinline__ void merge_full(const K *a, const K *b, K *dlo, K *dhi, uint32_t k)
 {
-    const uint32_t T = blockDim.x, tid = threadIdx.x;
-    K lo_v[IPT / 2], hi_v[IPT / 2];
+    constexpr int H2 = IPT / 2;
+    const uint32_t T = nmt(), tid = threadIdx.x;
+    {
+        // pairs (a[i], b[k-1-i]) for i in [tid*H2, tid*H2 + H2)
+        const uint32_t i0 = tid * H2;
+        K x[H2], yr[H2], lo[H2], hi[H2];
+        ld_run<K, H2>(a + i0, x);
+        ld_run<K, H2>(b + (k - i0 - H2), yr);
 #pragma unroll
-    for (int r = 0; r < IPT / 2; ++r) {
-        const uint32_t i = tid + r * T;
-        const K x = a[i], y = b[k - 1 - i];
-        lo_v[r] = x < y ? x : y;
-        hi_v[r] = x < y ? y : x;
+        for (int e = 0; e < H2; ++e) {
+            const K y = yr[H2 - 1 - e];
+            lo[e] = x[e] < y ? x[e] : y;
+            hi[e] = x[e] < y ? y : x[e];
+        }
+        bar_mg();
+        st_run<K, H2>(dlo + i0, lo);
+        st_run<K, H2>(dhi + i0, hi);
+        bar_mg();
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < IPT / 2; ++r) {
-        const uint32_t i = tid + r * T;
-        dlo[i] = lo_v[r];
-        dhi[i] = hi_v[r];
-    }
-    __syncthreads();
-    const uint32_t half = T >> 1;
+    (void)T;
+    const uint32_t half = nmt() >> 1;
     const uint32_t u = tid < half ? tid : tid - half;
     K *d = tid < half ? dlo : dhi;
     for (uint32_t st = k >> 1; st >= 32u * IPT; st >>= 1) {
+        // half-cleaner: thread u takes H2 adjacent pairs (l, l + st)
+        const uint32_t j = u * H2;
+        const uint32_t l = 2 * j - (j & (st - 1)), h = l + st;
+        K x[H2], y[H2];
+        ld_run<K, H2>(d + l, x);
+        ld_run<K, H2>(d + h, y);
 #pragma unroll
-        for (int r = 0; r < IPT / 2; ++r) {
-            const uint32_t j = u + r * half;
-            const uint32_t l = 2 * j - (j & (st - 1)), h = l + st;
-            const K x = d[l], y = d[h];
-            if (y < x) {
-                d[l] = y;
-                d[h] = x;
-            }
+        for (int e = 0; e < H2; ++e) {
+            const K mn = x[e] < y[e] ? x[e] : y[e];
+            const K mx = x[e] < y[e] ? y[e] : x[e];
+            x[e] = mn;
+            y[e] = mx;
         }
-        __syncthreads();
+        st_run<K, H2>(d + l, x);
+        st_run<K, H2>(d + h, y);
+        bar_mg();
     }
     K v[IPT];
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) v[q] = d[u * IPT + q];
+    ld_run<K, IPT>(d + u * IPT, v);
     const uint32_t lane = tid & 31u;
 #pragma unroll
     for (uint32_t lm = 16; lm >= 1; lm >>= 1) {
@@ -581,9 +677,8 @@ __device__ __forceinline__ void merge_full(const K *a, const K *b, K *dlo, K *dh
             }
         }
     }
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) d[u * IPT + q] = v[q];
-    __syncthreads();
+    st_run<K, IPT>(d + u * IPT, v);
+    bar_mg();
 }
 
 // MergeAndSort of two full k-runs into (k smallest -> dlo, k largest -> dhi):
@@ -591,25 +686,25 @@ __device__ __forceinline__ void merge_full(const K *a, const K *b, K *dlo, K *dh
 template <typename K, int IPT>
 __device__ __forceinline__ void merge_kk(const K *a, const K *b, K *dlo, K *dhi, uint32_t k)
 {
-    if (blockDim.x * IPT == 2 * k && k >= 32u * IPT) merge_full<K, IPT>(a, b, dlo, dhi, k);
+    if (nmt() * IPT == 2 * k && k >= 32u * IPT) merge_full<K, IPT>(a, b, dlo, dhi, k);
     else merge_split<K, IPT>(a, k, b, k, dlo, k, dhi);
 }
 
 // Takes a ticket under the root lock and records the operation in the
-// linearization record (thread 0).
+// linearization record (root holder only).
 template <typename K>
-__device__ __forceinline__ void take_ticket(const Params<K> &p, Shared &sh, uint32_t kind,
-                                            uint32_t n, unsigned long long ref)
+__device__ __forceinline__ void take_ticket(const Params<K> &p, const HeapView<K> &H, Shared &sh,
+                                            uint32_t kind, uint32_t n, unsigned long long ref)
 {
-    unsigned long long seq = __ldcg(&p.hdr->seq);
-    __stcg(&p.hdr->seq, seq + 1);
+    unsigned long long seq = __ldcg(&H.hdr->seq);
+    __stcg(&H.hdr->seq, seq + 1);
     sh.seq = seq;
-    if (seq < p.log_cap) {
+    if (seq < H.log_cap) {
         gheap_log_entry e;
         e.call_id = p.call_id;
         e.kind_n = (kind << 24) | n;
         e.ref = ref;
-        p.log[seq] = e;
+        H.log[seq] = e;
     }
 }
 
@@ -617,176 +712,253 @@ __device__ __forceinline__ void take_ticket(const Params<K> &p, Shared &sh, uint
 // INS (Section 3.2.2 top-down INS, Section 3.3.2 partial buffer)
 // ---------------------------------------------------------------------------
 
-// The batch a[0..n) is sorted (a[n..k) hold the key maximum).  Returns false
+// The batch PB(0)[0..n) is sorted (PB(0)[n..k) hold the key maximum) and the
+// block has met on a barrier since.  Buffers: 0 = the carried batch, 1 and 2
+// = the current and the next node, 3 = the partial buffer.  Returns false
 // when the operation had to give up (the block must stop).
 template <typename K, int IPT>
-__device__ bool ins_op(const Params<K> &p, Shared &sh, K *a, K *b, K *c, uint32_t n,
-                       unsigned long long ref)
+__device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
+                       uint32_t n, unsigned long long ref)
 {
     const uint32_t k = p.k;
-    const uint32_t tid = threadIdx.x;
+    const bool ctrl = is_ctrl();
+    const uint32_t lane = clane();
+    K *const A = base;                        // carry
+    K *const Bq = base + 3 * (size_t)k;       // partial buffer
+    K *root = H.keys + (size_t)k;
     long long tp = clock64();
-    if (tid == 0) {
-        unsigned long long w = 0;
-        sh.abort = !lock_root(p, sh, w);
-        if (!sh.abort) {
-            sh.t_root = gtimer();
-            sh.m = rw_m(w);
-            sh.s = rw_s(w);
-            take_ticket(p, sh, GHEAP_OP_INS, n, ref);
+
+    // take the root; for a full batch that goes down, mark the target, copy
+    // the root and try the first node of the path
+    if (ctrl) {
+        if (lane == 0) {
+            unsigned long long w = 0;
+            sh.abort = !lock_root(p, H, sh, w);
+            lap(sh, STAT_INS_ACQ_CYC, tp);
+            sh.tslot = 0;
+            if (!sh.abort) {
+                sh.t_root = gtimer();
+                const uint32_t m = rw_m(w), s = rw_s(w);
+                sh.m = m;
+                sh.s = s;
+                take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
+                const bool full = n == k || n + s >= k;
+                if (full && m >= 1) {
+                    if (m + 1 > H.max_nodes) {
+                        set_err(H, E_FULL);
+                        sh.abort = 1;
+                    } else {
+                        sh.tslot = m + 1;
+                        st_relaxed(&H.state[m + 1], ST_TARGET);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        const uint32_t tslot = sh.tslot;
+        if (tslot) {
+            g2s(base + (size_t)k, root, k, lane, 32u);   // root -> buffer 1
+            cp_async_commit();
+            if (lane == 0) {
+                const uint32_t tnode = slot_node(tslot);
+                const uint32_t n1 = tnode >> (level_of(tnode) - 1);
+                uint32_t *w1 = &H.state[slot_node(n1)];
+                sh.lk[0][0] = (n1 == tnode) ? claim_target(w1) : try_lock(w1);
+            }
+            cp_async_wait();
         }
     }
-    lap(sh, STAT_INS_ACQ_CYC, tp);
-    __syncthreads();
+    bar_all();
     if (sh.abort) return false;
     const uint32_t m = sh.m;
     uint32_t s = sh.s;
-    K *root = p.keys + (size_t)k;
 
-    if (n < k) {
-        // partial batch: merge into the partial buffer
-        const bool fits = n + s < k;
-        g2s_async(c, p.buf, s);
-        if (fits && m >= 1) g2s_async(b, root, k);
-        cp_async_commit();
-        cp_async_join();
-        if (fits) {
-            merge_split<K, IPT>(a, n, c, s, c, n + s, c);
-            if (m >= 1) {
-                // Property 3: the root keeps the k smallest of root + buffer
-                merge_split<K, IPT>(b, k, c, n + s, b, k, c);
-                s2g(root, b, k);
-                if (tid == 0) {
-                    stat_add(sh, STAT_LOADS, 1);
-                    stat_add(sh, STAT_STORES, 1);
-                    stat_add(sh, STAT_MERGES, 1);
+    if (!sh.tslot) {
+        // the batch stays at the root level: the partial buffer and/or a new
+        // root (no full node existed)
+        const bool fits = n < k && n + s < k;
+        if (!ctrl) {
+            if (n < k) {
+                g2s(Bq, H.buf, s, threadIdx.x, nmt());
+                if (fits && m >= 1) g2s(base + (size_t)k, root, k, threadIdx.x, nmt());
+                cp_async_commit();
+                cp_async_wait();
+                bar_mg();
+                if (fits) {
+                    merge_split<K, IPT>(A, n, Bq, s, Bq, n + s, Bq);
+                    if (m >= 1) {
+                        // Property 3: the root keeps the k smallest of root + buffer
+                        K *R = base + (size_t)k;
+                        merge_split<K, IPT>(R, k, Bq, n + s, R, k, Bq);
+                        s2g(root, R, k);
+                        if (threadIdx.x == 0) {
+                            stat_add(sh, STAT_LOADS, 1);
+                            stat_add(sh, STAT_STORES, 1);
+                            stat_add(sh, STAT_MERGES, 1);
+                        }
+                    }
+                    s2g(H.buf, Bq, n + s);
+                } else {
+                    // the k smallest of batch + buffer become the root (m == 0)
+                    merge_split<K, IPT>(A, n, Bq, s, A, k, Bq);
+                    s2g(H.buf, Bq, n + s - k);
                 }
+            } else if (s > 0) {
+                // a full batch becomes the root: keep Property 3 with the buffer
+                g2s(Bq, H.buf, s, threadIdx.x, nmt());
+                cp_async_commit();
+                cp_async_wait();
+                bar_mg();
+                merge_split<K, IPT>(A, k, Bq, s, A, k, Bq);
+                s2g(H.buf, Bq, s);
             }
-            s2g(p.buf, c, n + s);
-            if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root(p, m, n + s);
-            return true;
+            if (!fits) {
+                s2g(root, A, k);
+                if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+            }
         }
-        // the k smallest of batch + buffer go down as a full batch
-        merge_split<K, IPT>(a, n, c, s, a, k, c);
-        s = n + s - k;
-        s2g(p.buf, c, s);
-    } else if (m == 0 && s > 0) {
-        // the batch becomes the root: keep Property 3 with the buffer
-        g2s_async(c, p.buf, s);
-        cp_async_commit();
-        cp_async_join();
-        merge_split<K, IPT>(a, k, c, s, a, k, c);
-        s2g(p.buf, c, s);
-    }
-
-    if (m == 0) {
-        s2g(root, a, k);
-        if (tid == 0) {
-            stat_add(sh, STAT_STORES, 1);
+        bar_all();
+        if (ctrl && lane == 0) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            if (fits) release_root_word(H, m, n + s);
+            else release_root_word(H, 1u, n < k ? n + s - k : s);
         }
-        release_root(p, 1u, s);
         return true;
     }
 
-    // full top-down INS to the next target slot
-    const uint32_t tslot = m + 1;
-    if (tslot > p.max_nodes) {
-        if (tid == 0) set_err(p, E_FULL);
-        return false;
-    }
+    // full top-down INS to slot tslot
+    const uint32_t tslot = sh.tslot;
     const uint32_t tnode = slot_node(tslot);
     const uint32_t depth = level_of(tnode);
-    // the thread that later claims the target also marks it (program order)
-    if (tid == T2) st_relaxed(&p.state[tslot], ST_TARGET);
-
-    // root data, and a first try on the level-1 node of the path
-    g2s_async(b, root, k);
-    cp_async_commit();
-    if (tid == T2) {
-        const uint32_t n1 = tnode >> (depth - 1);
-        uint32_t *w1 = &p.state[slot_node(n1)];
-        sh.lk1 = (n1 == tnode) ? claim_target(w1) : try_lock(w1);
+    if (n < k) {
+        // overflow of the partial buffer: the k smallest go down
+        if (!ctrl) {
+            g2s(Bq, H.buf, s, threadIdx.x, nmt());
+            cp_async_commit();
+            cp_async_wait();
+            bar_mg();
+            merge_split<K, IPT>(A, n, Bq, s, A, k, Bq);
+            s2g(H.buf, Bq, n + s - k);
+        }
+        s = n + s - k;
     }
-    cp_async_join();
 
+    uint32_t ib = 1, ic = 2;       // current node, next node
     K *cur_keys = root;
-    uint32_t *cur_w = nullptr;   // nullptr = the root word
+    uint32_t *cur_w = nullptr;     // nullptr = the root word
+    uint32_t par = 0;
     for (uint32_t lvl = 0;; ++lvl) {
         const uint32_t nxt = tnode >> (depth - lvl - 1);
         const uint32_t nslot = slot_node(nxt);
-        uint32_t *nw = &p.state[nslot];
-        K *nkeys = p.keys + (size_t)nslot * k;
-        const bool at_target = (nxt == tnode);
-        // finish taking the next node (hand-over-hand: we hold the current one)
-        if (tid == T2) {
-            uint32_t v = sh.lk1;
-            if (at_target) {
-                sh.deliver = (v == ST_MARKED);
-                if (v != ST_TARGET && v != ST_MARKED) {
-                    set_err(p, E_STATE);
-                    sh.abort = 1;
+        uint32_t *nw = &H.state[nslot];
+        K *nkeys = H.keys + (size_t)nslot * k;
+        const bool at_target = nxt == tnode;
+        K *b = base + (size_t)ib * k;
+        K *c = base + (size_t)ic * k;
+        if (ctrl) {
+            // finish taking the next node (hand-over-hand: the current one is
+            // held); below the root also copy it now and try the one after
+            long long tw = clock64();
+            if (lane == 0) {
+                uint32_t v = sh.lk[par][0];
+                if (at_target) {
+                    sh.deliver = (v == ST_MARKED);
+                    if (v != ST_TARGET && v != ST_MARKED) {
+                        set_err(H, E_STATE);
+                        sh.abort = 1;
+                    }
+                } else if (v != ST_AVAIL) {
+                    v = lock_node(p, H, sh, nw, v);
+                    if (v != ST_AVAIL) {
+                        if (v != ST_GAVE_UP) set_err(H, E_STATE);
+                        sh.abort = 1;
+                    }
                 }
-            } else if (v != ST_AVAIL) {
-                v = lock_node(p, sh, nw, v);
-                if (v != ST_AVAIL) {
-                    if (v != ST_GAVE_UP) set_err(p, E_STATE);
-                    sh.abort = 1;
+            }
+            __syncwarp();
+            if (lvl > 0 && !at_target && !sh.abort) {
+                g2s(c, nkeys, k, lane, 32u);
+                cp_async_commit();
+                if (lane == 0) {
+                    const uint32_t n2 = tnode >> (depth - lvl - 2);
+                    uint32_t *w2 = &H.state[slot_node(n2)];
+                    sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
                 }
+                cp_async_wait();
             }
-        }
-        __syncthreads();
-        lap(sh, STAT_INS_WAIT_CYC, tp);
-        if (tid == 0) stat_add(sh, STAT_INS_LEVELS, 1);
-        if (sh.abort) return false;
-        uint32_t next_try = ST_EMPTY;
-        if (!at_target) {
-            g2s_async(c, nkeys, k);
-            cp_async_commit();
-            // try the node after next while this level merges
-            if (tid == T2) {
-                const uint32_t n2 = tnode >> (depth - lvl - 2);
-                uint32_t *w2 = &p.state[slot_node(n2)];
-                next_try = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+            if (lane == 0) {
+                lap(sh, STAT_INS_WAIT_CYC, tw);
+                stat_add(sh, STAT_INS_LEVELS, 1);
             }
-        }
-        // MergeAndSort(node, batch): the node keeps the k smallest, the k
-        // largest are carried on (Section 3.2.2); disjoint ranges are kept or
-        // swapped without merging (Section 4.3).
-        {
-            const K bmax = b[k - 1], bmin = b[0], amax = a[k - 1], amin = a[0];
-            if (bmax <= amin) {
-                if (tid == 0) stat_add(sh, STAT_SKIPS, 1);
-            } else if (amax <= bmin) {
-                s2g(cur_keys, a, k);
-                K *t = a; a = b; b = t;
-                if (tid == 0) { stat_add(sh, STAT_SKIPS, 1); stat_add(sh, STAT_STORES, 1); }
-            } else {
-                merge_kk<K, IPT>(b, a, b, a, k);
-                s2g(cur_keys, b, k);
-                if (tid == 0) { stat_add(sh, STAT_MERGES, 1); stat_add(sh, STAT_STORES, 1); }
-            }
-            if (tid == 0) stat_add(sh, STAT_LOADS, 1);
-        }
-        if (cur_w == nullptr) {
-            if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root(p, tslot, s);
         } else {
-            block_release(cur_w, ST_AVAIL);
+            // MergeAndSort(node, batch): the node keeps the k smallest, the k
+            // largest are carried on (Section 3.2.2); disjoint ranges are
+            // kept or swapped without merging (Section 4.3)
+            long long tm = clock64();
+            const K bmax = b[k - 1], bmin = b[0], amax = A[k - 1], amin = A[0];
+            bar_mg();
+            if (bmax <= amin) {
+                if (threadIdx.x == 0) stat_add(sh, STAT_SKIPS, 1);
+            } else if (amax <= bmin) {
+                // the node takes the batch; the old node keys are carried on
+                s2g(cur_keys, A, k);
+                bar_mg();
+                for (uint32_t i = threadIdx.x; i < k; i += nmt()) A[i] = b[i];
+                bar_mg();
+                if (threadIdx.x == 0) {
+                    stat_add(sh, STAT_SKIPS, 1);
+                    stat_add(sh, STAT_STORES, 1);
+                }
+            } else {
+                merge_kk<K, IPT>(b, A, b, A, k);
+                s2g(cur_keys, b, k);
+                if (threadIdx.x == 0) {
+                    stat_add(sh, STAT_MERGES, 1);
+                    stat_add(sh, STAT_STORES, 1);
+                }
+            }
+            if (threadIdx.x == 0) {
+                stat_add(sh, STAT_LOADS, 1);
+                lap(sh, STAT_INS_STEP_CYC, tm);
+            }
+        }
+        bar_all();
+        if (sh.abort) return false;
+        if (ctrl && lane == 0) {
+            if (cur_w == nullptr) {
+                stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                release_root_word(H, tslot, s);
+            } else {
+                st_release(cur_w, ST_AVAIL);
+            }
         }
         if (at_target) {
-            s2g(nkeys, a, k);
-            if (tid == 0) stat_add(sh, STAT_STORES, 1);
-            block_release(nw, sh.deliver ? ST_DELIVERED : ST_AVAIL);
+            if (!ctrl) {
+                s2g(nkeys, A, k);
+                if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+            }
+            bar_all();
+            if (ctrl && lane == 0) st_release(nw, sh.deliver ? ST_DELIVERED : ST_AVAIL);
             return true;
         }
-        if (tid == T2) sh.lk1 = next_try;
-        cp_async_join();
-        lap(sh, STAT_INS_STEP_CYC, tp);
-        K *t = b; b = c; c = t;
+        if (lvl == 0) {
+            // the root is released: now copy the level-1 node and try level 2
+            if (ctrl) {
+                g2s(c, nkeys, k, lane, 32u);
+                cp_async_commit();
+                if (lane == 0) {
+                    const uint32_t n2 = tnode >> (depth - 2);
+                    uint32_t *w2 = &H.state[slot_node(n2)];
+                    sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                }
+                cp_async_wait();
+            }
+            bar_all();
+        }
+        const uint32_t t = ib; ib = ic; ic = t;
         cur_keys = nkeys;
         cur_w = nw;
+        par ^= 1;
     }
 }
 
@@ -794,33 +966,56 @@ __device__ bool ins_op(const Params<K> &p, Shared &sh, K *a, K *b, K *c, uint32_
 // DEL (Section 3.2.1, partial buffer of Section 3.3.2)
 // ---------------------------------------------------------------------------
 
-// Children of `node` that exist in storage: slot numbers, or 0.
-__device__ __forceinline__ void child_slots(uint32_t node, uint32_t max_nodes, uint32_t &sl,
-                                            uint32_t &sr)
+// Control warp: lock the children (slots sl, sr; 0 = none) of a held node --
+// lane 0 the left, lane 1 the right, waiting as needed (`first0/1` are earlier
+// tries or NO_TRY) -- and copy the present ones into dl / dr.  Results go to
+// lk[0..1].  Returns with the copies complete.
+template <typename K>
+__device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapView<K> &H,
+                                                 Shared &sh, uint32_t sl, uint32_t sr,
+                                                 uint32_t first0, uint32_t first1, K *dl, K *dr,
+                                                 uint32_t *lk)
 {
-    const uint32_t l = 2 * node;
-    sl = sr = 0;
-    if (level_of(l) <= level_of(max_nodes)) {
-        uint32_t a = slot_node(l), b = slot_node(l + 1);
-        sl = a <= max_nodes ? a : 0;
-        sr = b <= max_nodes ? b : 0;
+    const uint32_t lane = clane();
+    const uint32_t k = p.k;
+    if (lane < 2) {
+        const uint32_t sx = lane ? sr : sl;
+        uint32_t v = ST_EMPTY;
+        if (sx) {
+            uint32_t f = lane ? first1 : first0;
+            if (f == NO_TRY) f = try_lock(&H.state[sx]);
+            v = lock_node(p, H, sh, &H.state[sx], f);
+        }
+        lk[lane] = v;
     }
+    __syncwarp();
+    if (lk[0] == ST_AVAIL) g2s(dl, H.keys + (size_t)sl * k, k, lane, 32u);
+    if (lk[1] == ST_AVAIL) g2s(dr, H.keys + (size_t)sr * k, k, lane, 32u);
+    cp_async_commit();
+    cp_async_wait();
 }
 
 // Deletes up to `want` keys.  MODE_DELETE takes its output offset and count
 // from the launch's running total under the root lock; MODE_OPS writes to
-// `out_off`.  Returns false when the block must stop.
+// `out_off`.  Six smem buffers rotate between the roles current node, left
+// and right child, and three free ones.  Returns false when the block must
+// stop.
 template <typename K, int IPT>
-__device__ bool del_op(const Params<K> &p, Shared &sh, K *A, K *B, K *C, K *D,
+__device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t want, unsigned long long out_off, unsigned long long ref,
                        uint32_t *count_out)
 {
     const uint32_t k = p.k;
-    const uint32_t tid = threadIdx.x;
+    const bool ctrl = is_ctrl();
+    const uint32_t lane = clane();
+    K *root = H.keys + (size_t)k;
     long long tp = clock64();
-    if (tid == 0) {
+#define PB(i) (base + (size_t)(i) * k)
+
+    // ---- take the root, the ticket and the output range
+    if (ctrl && lane == 0) {
         unsigned long long w = 0;
-        sh.abort = !lock_root(p, sh, w);
+        sh.abort = !lock_root(p, H, sh, w);
         lap(sh, STAT_DEL_ACQ_CYC, tp);
         if (!sh.abort) {
             sh.t_root = gtimer();
@@ -843,267 +1038,373 @@ __device__ bool del_op(const Params<K> &p, Shared &sh, K *A, K *B, K *C, K *D,
                 if (take == 0 || out_off + take >= p.n) p.ctl->drained = 1u;
             }
             if (count_out) *count_out = take;
-            take_ticket(p, sh, GHEAP_OP_DEL, take, p.mode == MODE_DELETE ? out_off : ref);
+            take_ticket(p, H, sh, GHEAP_OP_DEL, take, p.mode == MODE_DELETE ? out_off : ref);
         }
     }
-    __syncthreads();
+    bar_all();
     if (sh.abort) return false;
     const uint32_t m = sh.m, s = sh.s;
     const uint32_t take = sh.take;
     out_off = sh.out_off;
-    K *root = p.keys + (size_t)k;
 
     if (m == 0) {
         // no full node: serve from the partial buffer (Section 3.3.2)
-        g2s_async(C, p.buf, s);
-        cp_async_commit();
-        cp_async_join();
-        s2g(p.out + out_off, C, take);
-        s2g(p.buf, C + take, s - take);
-        if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-        release_root(p, 0u, s - take);
+        if (!ctrl) {
+            g2s(PB(5), H.buf, s, threadIdx.x, nmt());
+            cp_async_commit();
+            cp_async_wait();
+            bar_mg();
+            s2g(p.out + out_off, PB(5), take);
+            s2g(H.buf, PB(5) + take, s - take);
+        }
+        bar_all();
+        if (ctrl && lane == 0) {
+            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            release_root_word(H, 0u, s - take);
+        }
         return true;
     }
 
-    // the root refill needs the last node when the buffer cannot supply take
     const bool need_last = s < take && m >= 2;
-    g2s_async(B, root, k);
-    g2s_async(C, p.buf, s);
-    cp_async_commit();
-    if (need_last && tid == T2) sh.lk1 = try_lock(&p.state[m]);
-    cp_async_join();
-    s2g(p.out + out_off, B, take);
-    if (tid == 0) stat_add(sh, STAT_LOADS, 1);
-    uint32_t nm = m, ns;
-    if (s >= take) {
-        // refill the root from the partial buffer
-        merge_split<K, IPT>(B + take, k - take, C, s, B, k, C);
-        ns = s - take;
-        s2g(p.buf, C, ns);
-    } else {
-        const uint32_t tn = k - take + s;
-        merge_split<K, IPT>(B + take, k - take, C, s, C, tn, C);
-        if (m == 1) {
-            // the root was the last full node
-            s2g(p.buf, C, tn);
-            if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root(p, 0u, tn);
-            return true;
-        }
-        // refill the root from the last node (slot m)
-        uint32_t *lw = &p.state[m];
-        if (tid == T2) {
-            if (take_last(p, sh, lw, sh.lk1)) {
-                // nobody may lock or target slot m until the root is released
-                st_relaxed(lw, ST_EMPTY);
-            } else {
-                sh.abort = 1;
-            }
-        } else if (tid >= 64 && tid < 96 && m >= 3) {
-            // the next DEL's last node: warm L2 (one 128-byte line a thread)
-            const char *nxt = reinterpret_cast<const char *>(p.keys + (size_t)(m - 1) * k);
-            for (uint32_t off = (tid - 64) * 128u; off < k * sizeof(K); off += 32 * 128u)
-                prefetch_l2(nxt + off);
-        }
-        __syncthreads();
-        if (sh.abort) return false;
-        if (tn == 0) {
-            // nothing left of the root or the buffer: the last node is the root
-            g2s_async(B, p.keys + (size_t)m * k, k);
-            cp_async_commit();
-            cp_async_join();
-        } else {
-            g2s_async(A, p.keys + (size_t)m * k, k);
-            cp_async_commit();
-            cp_async_join();
-            merge_split<K, IPT>(C, tn, A, k, B, k, C);
-        }
-        if (tid == 0) stat_add(sh, STAT_LOADS, 1);
-        ns = tn;
-        nm = m - 1;
-        s2g(p.buf, C, ns);
-    }
+    const bool root_gone = s < take && m == 1;
+    const uint32_t tn = k - take + s;             // root + buffer keys left (when s < take)
+    uint32_t ic = 0, il = 1, ir = 2, f1 = 3, f2 = 4;   // buffer 5 holds the partial buffer
 
-    // sift down from the root; B holds the current node's keys
+    // ---- root step.  Merge threads: root and buffer in, output, first part
+    // of the refill.  Control warp: the last node, then the root's children.
+    if (!ctrl) {
+        g2s(PB(ic), root, k, threadIdx.x, nmt());
+        g2s(PB(5), H.buf, s, threadIdx.x, nmt());
+        cp_async_commit();
+        cp_async_wait();
+        bar_mg();
+        s2g(p.out + out_off, PB(ic), take);
+        if (threadIdx.x == 0) stat_add(sh, STAT_LOADS, 1);
+        if (s >= take) {
+            merge_split<K, IPT>(PB(ic) + take, k - take, PB(5), s, PB(ic), k, PB(5));
+            s2g(H.buf, PB(5), s - take);
+        } else {
+            merge_split<K, IPT>(PB(ic) + take, k - take, PB(5), s, PB(5), tn, PB(5));
+            if (root_gone) s2g(H.buf, PB(5), tn);
+        }
+    } else if (!root_gone) {
+        uint32_t sl, sr;
+        child_slots(1, H.max_nodes, sl, sr);
+        if (need_last) {
+            uint32_t *lw = &H.state[m];
+            if (m <= 3) {
+                // the last node is a child of the root: take it first, then
+                // lock the other child (the taken one reads EMPTY)
+                if (lane == 0) {
+                    if (take_last(p, H, sh, lw, try_lock(lw))) st_relaxed(lw, ST_EMPTY);
+                    else sh.abort = 1;
+                }
+                __syncwarp();
+                if (!sh.abort) g2s(PB(f1), H.keys + (size_t)m * k, k, lane, 32u);
+                cp_async_commit();
+                cw_take_children(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir), sh.lk[0]);
+            } else {
+                // try the last node and both children at once.  An INS still
+                // in flight to the last node may need a child of the root, so
+                // the children are given back while the DEL waits for it.
+                uint32_t t = ST_EMPTY;
+                if (lane == 2) t = try_lock(lw);
+                if (lane < 2) t = try_lock(&H.state[lane ? sr : sl]);
+                const uint32_t tl = __shfl_sync(0xffffffffu, t, 2);
+                const bool inflight = tl != ST_AVAIL && tl != ST_INUSE;
+                if (inflight && lane < 2 && t == ST_AVAIL)
+                    st_release(&H.state[lane ? sr : sl], ST_AVAIL);
+                if (lane == 2) {
+                    if (take_last(p, H, sh, lw, tl)) st_relaxed(lw, ST_EMPTY);
+                    else sh.abort = 1;
+                }
+                __syncwarp();
+                if (!sh.abort) g2s(PB(f1), H.keys + (size_t)m * k, k, lane, 32u);
+                cp_async_commit();
+                const uint32_t c0 = __shfl_sync(0xffffffffu, t, 0);
+                const uint32_t c1 = __shfl_sync(0xffffffffu, t, 1);
+                cw_take_children(p, H, sh, sl, sr, inflight ? NO_TRY : c0,
+                                 inflight ? NO_TRY : c1, PB(il), PB(ir), sh.lk[0]);
+            }
+        } else {
+            cw_take_children(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir), sh.lk[0]);
+        }
+    }
+    bar_all();
+    if (sh.abort) return false;
+    if (root_gone) {
+        if (ctrl && lane == 0) {
+            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            release_root_word(H, 0u, tn);
+        }
+        return true;
+    }
+    uint32_t nm = m;
+    const uint32_t ns = s >= take ? s - take : tn;
+    if (need_last) {
+        nm = m - 1;
+        if (tn > 0) {
+            if (!ctrl) {
+                merge_split<K, IPT>(PB(5), tn, PB(f1), k, PB(ic), k, PB(5));
+                s2g(H.buf, PB(5), tn);
+            }
+        } else {
+            // nothing of the root or buffer is left: the last node is the root
+            const uint32_t t = ic; ic = f1; f1 = t;
+        }
+        if (!ctrl && threadIdx.x == 0) stat_add(sh, STAT_LOADS, 1);
+    }
+    bar_all();
+    if (ctrl && lane == 0) lap(sh, STAT_DEL_ROOT_CYC, tp);
+
+    // ---- sift down (Section 3.2.1).  At the top of every level the block
+    // has met: the current node's keys are in PB(ic), its children's lock
+    // results in sh.lk[par] and their keys in PB(il), PB(ir).
     uint32_t node = 1;
     K *cur_keys = root;
-    uint32_t *cur_w = nullptr;       // nullptr = the root word
-    uint32_t tried0 = 0, tried1 = 0; // earlier tries on the children
-    bool pre = false;
-    lap(sh, STAT_DEL_ROOT_CYC, tp);
+    uint32_t *cur_w = nullptr;   // nullptr = the root word
+    uint32_t par = 0;
     for (;;) {
-        uint32_t sl, sr;
-        child_slots(node, p.max_nodes, sl, sr);
-        // lock both children at once (thread 0: left, thread T2: right)
-        if (tid == 0) {
-            uint32_t v = sl ? (pre ? tried0 : try_lock(&p.state[sl])) : ST_EMPTY;
-            if (sl) v = lock_node(p, sh, &p.state[sl], v);
-            sh.lk0 = v;
-        } else if (tid == T2) {
-            uint32_t v = sr ? (pre ? tried1 : try_lock(&p.state[sr])) : ST_EMPTY;
-            if (sr) v = lock_node(p, sh, &p.state[sr], v);
-            sh.lk1 = v;
-        }
-        __syncthreads();
-        lap(sh, STAT_DEL_WAIT_CYC, tp);
-        if (tid == 0) stat_add(sh, STAT_DEL_LEVELS, 1);
-        if (sh.lk0 == ST_GAVE_UP || sh.lk1 == ST_GAVE_UP) return false;
-        const bool pl = sh.lk0 == ST_AVAIL, pr = sh.lk1 == ST_AVAIL;
+        const uint32_t lk0 = sh.lk[par][0], lk1 = sh.lk[par][1];
+        if (lk0 == ST_GAVE_UP || lk1 == ST_GAVE_UP) return false;
+        const bool pl = lk0 == ST_AVAIL, pr = lk1 == ST_AVAIL;
         if (!pl && !pr) break;
-        K *lk = p.keys + (size_t)sl * k;
-        K *rk = p.keys + (size_t)sr * k;
-        if (pl) g2s_async(C, lk, k);
-        if (pr) g2s_async(D, rk, k);
-        cp_async_commit();
-        cp_async_join();
-        lap(sh, STAT_DEL_LOAD_CYC, tp);
-        if (tid == 0) stat_add(sh, STAT_LOADS, (unsigned long long)(pl + pr));
-        const K cmax = B[k - 1];
+        uint32_t sl, sr;
+        child_slots(node, H.max_nodes, sl, sr);
+        K *const Bc = PB(ic);
+        K *const C = PB(il);
+        K *const D = PB(ir);
+        const K cmax = Bc[k - 1];
+        const K c0 = C[0], ck = C[k - 1], d0 = D[0], dk = D[k - 1];
+        if (ctrl && lane == 0) stat_add(sh, STAT_DEL_LEVELS, 1);
+        bar_all();   // everybody has read the decision inputs
+        const bool at_root = cur_w == nullptr;
+        // the next DEL waits on this DEL's level-1 node rather than on the
+        // root, so the next level is prefetched during the merges at every
+        // level, the root included
+        const bool defer = false;
+
         if (pl != pr) {
             // one child present (the other is absent or an INS target)
-            K *X = pl ? C : D;
-            uint32_t *xw = &p.state[pl ? sl : sr];
-            if (cmax <= X[0]) {
-                block_release(xw, ST_AVAIL);
+            const bool usel = pl;
+            const uint32_t xs = usel ? sl : sr;
+            uint32_t *xw = &H.state[xs];
+            K *xk = H.keys + (size_t)xs * k;
+            if (cmax <= (usel ? c0 : d0)) {
+                if (ctrl && lane == 0) st_release(xw, ST_AVAIL);
                 break;
             }
-            const uint32_t x = pl ? 2 * node : 2 * node + 1;
+            const uint32_t x = 2 * node + (usel ? 0 : 1);
             uint32_t gl, gr;
-            child_slots(x, p.max_nodes, gl, gr);
-            uint32_t t_try0 = ST_EMPTY, t_try1 = ST_EMPTY;
-            if (tid == 0 && gl) t_try0 = try_lock(&p.state[gl]);
-            if (tid == T2 && gr) t_try1 = try_lock(&p.state[gr]);
-            merge_kk<K, IPT>(B, X, B, X, k);
-            lap(sh, STAT_DEL_MERGE_CYC, tp);
-            s2g(cur_keys, B, k);
-            if (tid == 0) {
-                stat_add(sh, STAT_MERGES, 1);
-                stat_add(sh, STAT_STORES, 1);
+            child_slots(x, H.max_nodes, gl, gr);
+            K *const X = usel ? C : D;
+            if (!ctrl) {
+                long long tm = clock64();
+                merge_kk<K, IPT>(Bc, X, Bc, X, k);
+                s2g(cur_keys, Bc, k);
+                if (threadIdx.x == 0) {
+                    stat_add(sh, STAT_MERGES, 1);
+                    stat_add(sh, STAT_STORES, 1);
+                    lap(sh, STAT_DEL_MERGE_CYC, tm);
+                }
+            } else if (!defer) {
+                long long tw = clock64();
+                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
+                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
             }
-            if (cur_w == nullptr) {
-                if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                release_root(p, nm, ns);
-            } else {
-                block_release(cur_w, ST_AVAIL);
+            bar_all();
+            if (ctrl) {
+                if (lane == 0) {
+                    long long tr = clock64();
+                    if (at_root) {
+                        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                        release_root_word(H, nm, ns);
+                    } else {
+                        st_release(cur_w, ST_AVAIL);
+                    }
+                    lap(sh, STAT_DEL_REL_CYC, tr);
+                }
+                __syncwarp();
+                if (defer) {
+                    long long tw = clock64();
+                    cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
+                                     sh.lk[par ^ 1]);
+                    if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
+                }
             }
-            lap(sh, STAT_DEL_REL_CYC, tp);
-            tried0 = t_try0;
-            tried1 = t_try1;
-            pre = true;
+            if (defer) bar_all();
+            const uint32_t xb = usel ? il : ir, ob = usel ? ir : il;
+            const uint32_t n1 = ic, n2 = ob;
+            ic = xb; il = f1; ir = f2; f1 = n1; f2 = n2;
             node = x;
-            cur_keys = pl ? lk : rk;
+            cur_keys = xk;
             cur_w = xw;
-            K *t = B; B = X;
-            if (pl) C = t; else D = t;
+            par ^= 1;
             continue;
         }
+
         // both children present
-        if (cmax <= C[0] && cmax <= D[0]) {
+        if (cmax <= c0 && cmax <= d0) {
             // early stop (Section 4.3)
-            if (tid == 0) st_release(&p.state[sl], ST_AVAIL);
-            if (tid == T2) st_release(&p.state[sr], ST_AVAIL);
+            if (ctrl && lane < 2) st_release(&H.state[lane ? sr : sl], ST_AVAIL);
             break;
         }
-        // MergeAndSort(l, r): the k largest go to the child whose maximum
-        // was larger (the right child on a tie), the k smallest to the other
-        const bool big_l = C[k - 1] > D[k - 1];
+        // MergeAndSort(l, r): the k largest go to the child whose maximum was
+        // larger (the right child on a tie), the k smallest to the other
+        const bool big_l = ck > dk;
         const uint32_t smn = big_l ? 2 * node + 1 : 2 * node;
         uint32_t gl, gr;
-        child_slots(smn, p.max_nodes, gl, gr);
-        uint32_t t_try0 = ST_EMPTY, t_try1 = ST_EMPTY;
-        if (tid == 0 && gl) t_try0 = try_lock(&p.state[gl]);
-        if (tid == T2 && gr) t_try1 = try_lock(&p.state[gr]);
-        K *S, *L;               // smem of the small and large halves
-        bool l_changed, r_changed;
-        if (C[k - 1] <= D[0]) {
-            S = C; L = D;
+        child_slots(smn, H.max_nodes, gl, gr);
+        bool S_is_C, l_changed, r_changed;
+        const bool overlap = ck > d0 && dk > c0;
+        if (ck <= d0) {
+            S_is_C = true;
             l_changed = r_changed = big_l;   // false here: nothing moves
-        } else if (D[k - 1] <= C[0]) {
-            S = D; L = C;
+        } else if (dk <= c0) {
+            S_is_C = false;
             l_changed = r_changed = !big_l;
         } else {
-            merge_kk<K, IPT>(C, D, C, D, k);
-            S = C; L = D;
+            S_is_C = true;
             l_changed = r_changed = true;
-            if (tid == 0) stat_add(sh, STAT_MERGES, 1);
         }
-        lap(sh, STAT_DEL_MERGE_CYC, tp);
-        if (!l_changed && tid == 0) stat_add(sh, STAT_SKIPS, 1);
-        K *big_keys = big_l ? lk : rk;
-        uint32_t *big_w = &p.state[big_l ? sl : sr];
-        K *sm_keys = big_l ? rk : lk;
-        uint32_t *sm_w = &p.state[big_l ? sr : sl];
+        K *const S = S_is_C ? C : D;
+        K *const L = S_is_C ? D : C;
+        const uint32_t bigs = big_l ? sl : sr, sms = big_l ? sr : sl;
+        K *big_keys = H.keys + (size_t)bigs * k;
+        K *sm_keys = H.keys + (size_t)sms * k;
+        uint32_t *big_w = &H.state[bigs];
+        uint32_t *sm_w = &H.state[sms];
         const bool big_changed = big_l ? l_changed : r_changed;
         const bool sm_changed = big_l ? r_changed : l_changed;
-        if (big_changed) {
-            s2g(big_keys, L, k);
-            if (tid == 0) stat_add(sh, STAT_STORES, 1);
-        }
-        block_release(big_w, ST_AVAIL);
-        lap(sh, STAT_DEL_REL_CYC, tp);
-        if (cmax <= S[0]) {
-            if (sm_changed) {
-                s2g(sm_keys, S, k);
-                if (tid == 0) stat_add(sh, STAT_STORES, 1);
+        uint32_t t_try = ST_EMPTY;
+        if (!ctrl) {
+            long long tm = clock64();
+            if (overlap) {
+                merge_kk<K, IPT>(C, D, C, D, k);
+                if (threadIdx.x == 0) stat_add(sh, STAT_MERGES, 1);
+            } else if (threadIdx.x == 0) {
+                stat_add(sh, STAT_SKIPS, 1);
             }
-            // give back the grandchildren taken by the tries
-            if (tid == 0 && t_try0 == ST_AVAIL) st_release(&p.state[gl], ST_AVAIL);
-            if (tid == T2 && t_try1 == ST_AVAIL) st_release(&p.state[gr], ST_AVAIL);
-            block_release(sm_w, ST_AVAIL);
+            if (big_changed) {
+                s2g(big_keys, L, k);
+                if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+            }
+            if (threadIdx.x == 0) {
+                sh.halt = cmax <= S[0];
+                lap(sh, STAT_DEL_MERGE_CYC, tm);
+            }
+        } else if (!defer && lane < 2) {
+            // try the small child's children while the merge threads work
+            const uint32_t gx = lane ? gr : gl;
+            if (gx) t_try = try_lock(&H.state[gx]);
+        }
+        bar_all();
+        const bool halt = sh.halt;
+        if (ctrl) {
+            if (lane == 0) {
+                long long tr = clock64();
+                st_release(big_w, ST_AVAIL);
+                lap(sh, STAT_DEL_REL_CYC, tr);
+            }
+            if (!defer) {
+                if (halt) {
+                    // the sift ends here: give back what the tries took
+                    if (lane < 2 && t_try == ST_AVAIL)
+                        st_release(&H.state[lane ? gr : gl], ST_AVAIL);
+                } else {
+                    long long tw = clock64();
+                    const uint32_t t0 = __shfl_sync(0xffffffffu, t_try, 0);
+                    const uint32_t t1 = __shfl_sync(0xffffffffu, t_try, 1);
+                    cw_take_children(p, H, sh, gl, gr, gl ? t0 : NO_TRY, gr ? t1 : NO_TRY,
+                                     PB(f1), PB(f2), sh.lk[par ^ 1]);
+                    if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
+                }
+            }
+        } else {
+            long long tm = clock64();
+            if (halt) {
+                if (sm_changed) {
+                    s2g(sm_keys, S, k);
+                    if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+                }
+            } else {
+                // MergeAndSort(cur, small child): cur keeps the k smallest
+                merge_kk<K, IPT>(Bc, S, Bc, S, k);
+                s2g(cur_keys, Bc, k);
+                if (threadIdx.x == 0) {
+                    stat_add(sh, STAT_MERGES, 1);
+                    stat_add(sh, STAT_STORES, 1);
+                }
+            }
+            if (threadIdx.x == 0) lap(sh, STAT_DEL_MERGE_CYC, tm);
+        }
+        bar_all();
+        if (halt) {
+            if (ctrl && lane == 0) st_release(sm_w, ST_AVAIL);
             break;
         }
-        // MergeAndSort(cur, small child): cur keeps the k smallest
-        merge_kk<K, IPT>(B, S, B, S, k);
-        lap(sh, STAT_DEL_MERGE_CYC, tp);
-        s2g(cur_keys, B, k);
-        if (tid == 0) {
-            stat_add(sh, STAT_MERGES, 1);
-            stat_add(sh, STAT_STORES, 1);
+        if (ctrl) {
+            if (lane == 0) {
+                long long tr = clock64();
+                if (at_root) {
+                    stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                    release_root_word(H, nm, ns);
+                } else {
+                    st_release(cur_w, ST_AVAIL);
+                }
+                lap(sh, STAT_DEL_REL_CYC, tr);
+            }
+            __syncwarp();
+            if (defer) {
+                long long tw = clock64();
+                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
+                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
+            }
         }
-        if (cur_w == nullptr) {
-            if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root(p, nm, ns);
-        } else {
-            block_release(cur_w, ST_AVAIL);
-        }
-        lap(sh, STAT_DEL_REL_CYC, tp);
-        tried0 = t_try0;
-        tried1 = t_try1;
-        pre = true;
+        if (defer) bar_all();
+        const uint32_t sb = S_is_C ? il : ir, lb = S_is_C ? ir : il;
+        const uint32_t n1 = ic, n2 = lb;
+        ic = sb; il = f1; ir = f2; f1 = n1; f2 = n2;
         node = smn;
         cur_keys = sm_keys;
         cur_w = sm_w;
-        K *oldB = B;
-        B = S;
-        if (S == C) C = oldB; else D = oldB;
+        par ^= 1;
     }
     // last node of the walk: write it and release it
-    s2g(cur_keys, B, k);
-    if (tid == 0) stat_add(sh, STAT_STORES, 1);
-    if (cur_w == nullptr) {
-        if (tid == 0) stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-        release_root(p, nm, ns);
-    } else {
-        block_release(cur_w, ST_AVAIL);
+    if (!ctrl) {
+        s2g(cur_keys, PB(ic), k);
+        if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
     }
-    (void)A;
+    bar_all();
+    if (ctrl && lane == 0) {
+        if (cur_w == nullptr) {
+            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            release_root_word(H, nm, ns);
+        } else {
+            st_release(cur_w, ST_AVAIL);
+        }
+    }
     return true;
+#undef PB
 }
 
 // ---------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------
 
+// Block size bound per merge width: 512 merge threads + the control warp for
+// IPT <= 4, 256 + 32 for wider merges (fewer warps, more registers each).
+template <int IPT>
+struct MaxThreads { static constexpr int value = IPT >= 8 ? 288 : 544; };
+
 template <typename K, int IPT>
-__global__ void __launch_bounds__(512, 1) heap_kernel(Params<K> p)
+__global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<K> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared sh;
     const uint32_t k = p.k;
-    K *A = reinterpret_cast<K *>(smem_raw);
-    K *B = A + k;
-    K *C = B + k;
-    K *D = C + k;
+    K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
+    const HeapView<K> &H = p.h;
     if (threadIdx.x < N_STATS) sh.cnt[threadIdx.x] = 0;
 
     unsigned long long n_ops;
@@ -1114,12 +1415,13 @@ __global__ void __launch_bounds__(512, 1) heap_kernel(Params<K> p)
         if (threadIdx.x == 0) {
             unsigned long long op = atomicAdd(&p.ctl->next_op, 1ull);
             sh.op = op;
-            int stop = op >= n_ops || ld_relaxed(&p.hdr->err) != E_NONE;
+            int stop = op >= n_ops || ld_relaxed(&H.hdr->err) != E_NONE;
             if (!stop && p.mode == MODE_DELETE && ld_relaxed(&p.ctl->drained)) stop = 1;
             sh.stop = stop;
             sh.abort = 0;
+            sh.halt = 0;
         }
-        __syncthreads();
+        bar_all();
         if (sh.stop) break;
         const unsigned long long op = sh.op;
         bool ok;
@@ -1141,33 +1443,36 @@ __global__ void __launch_bounds__(512, 1) heap_kernel(Params<K> p)
         }
         if (kind == GHEAP_OP_INS) {
             // stage and sort the batch before taking the root (Section 4.1)
-            long long ts = clock64();
-            const K *src = p.in + off;
-            if (n < k) {
-                for (uint32_t i = threadIdx.x; i < k; i += blockDim.x)
-                    A[i] = i < n ? __ldcg(src + i) : kmax<K>();
-                __syncthreads();
-            } else {
-                g2s_async(A, src, k);
-                cp_async_commit();
-                cp_async_join();
+            if (!is_ctrl()) {
+                long long ts = clock64();
+                const K *src = p.in + off;
+                if (n < k) {
+                    for (uint32_t i = threadIdx.x; i < k; i += nmt())
+                        base[i] = i < n ? __ldcg(src + i) : kmax<K>();
+                } else {
+                    g2s(base, src, k, threadIdx.x, nmt());
+                    cp_async_commit();
+                    cp_async_wait();
+                }
+                bar_mg();
+                block_sort(base, k);
+                if (threadIdx.x == 0) lap(sh, STAT_INS_SORT_CYC, ts);
             }
-            block_sort(A, k);
-            lap(sh, STAT_INS_SORT_CYC, ts);
-            ok = ins_op<K, IPT>(p, sh, A, B, C, n, p.mode == MODE_OPS ? op : off);
+            bar_all();
+            ok = ins_op<K, IPT>(p, H, sh, base, n, p.mode == MODE_OPS ? op : off);
             if (threadIdx.x == 0) {
                 stat_add(sh, STAT_INS, 1);
                 if (p.mode == MODE_OPS && p.out_counts) p.out_counts[op] = n;
             }
         } else {
-            ok = del_op<K, IPT>(p, sh, A, B, C, D, n, off, op,
+            ok = del_op<K, IPT>(p, H, sh, base, n, off, op,
                                 p.mode == MODE_OPS && p.out_counts ? p.out_counts + op : nullptr);
             if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
         }
         if (!ok) break;
-        __syncthreads();
+        bar_all();
     }
-    __syncthreads();
+    bar_all();
     if (p.stats && threadIdx.x < N_STATS && sh.cnt[threadIdx.x])
         atomicAdd(p.stats + threadIdx.x, sh.cnt[threadIdx.x]);
 }

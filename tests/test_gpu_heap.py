@@ -88,7 +88,7 @@ def test_single_cta_random_calls_match_model(k, key_bytes):
     rng = np.random.default_rng(1000 + k + key_bytes)
     cap = 40 * k + 7
     with GHeap(capacity=cap, k=k, key_bytes=key_bytes, log_capacity=4096) as h:
-        h.set_launch(ctas=1, items_per_thread=8 if k >= 2048 else 4)
+        h.set_launch(ctas=1, items_per_thread=16 if k >= 2048 else 4)
         model = GeneralizedHeapModel(k, dtype=np_dtype(key_bytes))
         r = Recorder(h)
         size = 0
