@@ -172,6 +172,69 @@ int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
  * completing.  The paper has no counterpart; heap_reset() undoes it. */
 int heap_debug_hold_root(gheap_t h, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Heap sets: many independent heaps driven by one persistent launch.
+ *
+ * Each heap of a set is an ordinary generalized heap with its own root lock,
+ * so operations on different heaps never wait for each other; operations on
+ * the same heap are linearized by that heap's root as for a single heap
+ * (Section 3.3.3).  One launch runs a list of operations that name their
+ * heap; the persistent thread blocks take them in list order.
+ * ------------------------------------------------------------------------ */
+
+typedef struct gheapset_s *gheapset_t;
+
+/* One operation of heapset_ops: heap index, kind_n = (GHEAP_OP_INS or
+ * GHEAP_OP_DEL) << 24 | n (1..k), and the key offset into the launch's
+ * input (INS) or output (DEL) array. */
+typedef struct {
+    uint32_t heap;
+    uint32_t kind_n;
+    uint64_t offset;
+} gheapset_op;
+
+/* Creates n_heaps empty heaps; capacities[i] (host array) is heap i's
+ * capacity in keys.  k, key_bytes, flags and log_capacity (per heap) as for
+ * heap_create.  All heaps live on the current device. */
+int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities, uint32_t k,
+                   uint32_t key_bytes, uint32_t flags, uint64_t log_capacity);
+
+/* Frees every heap of the set (synchronizes the device first). */
+int heapset_destroy(gheapset_t s);
+
+/* Heap i of the set, for the single-heap queries (heap_size, heap_get_log,
+ * heap_snapshot, heap_get_stats, heap_reset).  Owned by the set. */
+gheap_t heapset_heap(gheapset_t s, uint32_t i);
+
+/* Launch shape and wait bound, as heap_set_launch / heap_set_timeout. */
+int heapset_set_launch(gheapset_t s, uint32_t ctas, uint32_t items_per_thread);
+int heapset_set_timeout(gheapset_t s, uint64_t ns);
+
+/* Runs d_ops[0..n_ops) (device gheapset_op array) in one persistent launch.
+ * INS reads keys from d_in_keys[offset..], DEL writes the keys it removes,
+ * ascending, to d_out_keys[offset..] and its count to d_out_counts[i]
+ * (INS: n, or 0 when skipped).  An op whose heap already holds a sticky
+ * error is skipped; an insert beyond a heap's node storage sets that heap's
+ * GHEAP_ERR_FULL.  Capacities are not checked on the host. */
+int heapset_ops(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops, const void *d_in_keys,
+                void *d_out_keys, uint32_t *d_out_counts, void *stream);
+
+/* Waits for the device and returns the first sticky error of any heap. */
+int heapset_sync(gheapset_t s);
+
+/* Empties every heap and clears their records and errors (on `stream`). */
+int heapset_reset(gheapset_t s, void *stream);
+
+/* CUDA-graph form of heapset_ops: records the launch for the given arrays
+ * once (stream capture) and replays it with heapset_graph_launch; the arrays
+ * must stay valid while the graph exists. */
+typedef struct gheapset_graph_s *gheapset_graph_t;
+int heapset_graph_create(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops,
+                         const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
+                         gheapset_graph_t *out);
+int heapset_graph_launch(gheapset_graph_t g, void *stream);
+int heapset_graph_destroy(gheapset_graph_t g);
+
 /* Human-readable text of an error code. */
 const char *heap_strerror(int code);
 

@@ -63,37 +63,55 @@ uint32_t threads_for(uint32_t k, uint32_t ipt) { return merge_threads_for(k, ipt
 // Merge threads allowed by the kernel's launch bound for this merge width.
 uint32_t max_merge_threads(uint32_t ipt) { return ipt >= 8 ? 256 : 512; }
 
+// What a launch needs besides the kernel parameters.
+struct Shape {
+    uint32_t k, ipt, ctas;
+    int sm_count;
+    gh::Ctl *d_ctl;
+};
+
 template <typename K, int IPT>
-int launch_t(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
+int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
     auto kern = gh::heap_kernel<K, IPT>;
-    const uint32_t threads = threads_for(h->k, IPT);
-    const size_t smem = 6u * (size_t)h->k * sizeof(K);
+    const uint32_t threads = threads_for(sp.k, IPT);
+    const size_t smem = 6u * (size_t)sp.k * sizeof(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return GHEAP_ERR_CUDA;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
     if (e != cudaSuccess || per_sm < 1) return GHEAP_ERR_CUDA;
-    uint64_t grid = h->ctas ? h->ctas : (uint64_t)per_sm * h->sm_count;
-    if (grid > (uint64_t)per_sm * h->sm_count) grid = (uint64_t)per_sm * h->sm_count;
+    uint64_t grid = sp.ctas ? sp.ctas : (uint64_t)per_sm * sp.sm_count;
+    if (grid > (uint64_t)per_sm * sp.sm_count) grid = (uint64_t)per_sm * sp.sm_count;
     if (grid > n_ops) grid = n_ops;
     if (grid == 0) return GHEAP_OK;
-    e = cudaMemsetAsync(h->d_ctl, 0, sizeof(gh::Ctl), s);
+    e = cudaMemsetAsync(sp.d_ctl, 0, sizeof(gh::Ctl), s);
     if (e != cudaSuccess) return GHEAP_ERR_CUDA;
     kern<<<(unsigned)grid, threads, smem, s>>>(p);
     return cuda_err(cudaGetLastError());
 }
 
 template <typename K>
-int launch_k(gheap_t h, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
+int launch_k(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
-    switch (h->ipt) {
-    case 4: return launch_t<K, 4>(h, p, n_ops, s);
-    case 8: return launch_t<K, 8>(h, p, n_ops, s);
-    case 16: return launch_t<K, 16>(h, p, n_ops, s);
+    switch (sp.ipt) {
+    case 4: return launch_t<K, 4>(sp, p, n_ops, s);
+    case 8: return launch_t<K, 8>(sp, p, n_ops, s);
+    case 16: return launch_t<K, 16>(sp, p, n_ops, s);
     default: return GHEAP_ERR_ARG;
     }
+}
+
+Shape shape_of(gheap_t h)
+{
+    Shape sp;
+    sp.k = h->k;
+    sp.ipt = h->ipt;
+    sp.ctas = h->ctas;
+    sp.sm_count = h->sm_count;
+    sp.d_ctl = h->d_ctl;
+    return sp;
 }
 
 template <typename K>
@@ -131,7 +149,7 @@ int launch(gheap_t h, uint32_t mode, const void *in, void *out, uint64_t n,
         p.n_ops = n_ops;
         p.out_counts = out_counts;
         p.out_total = reinterpret_cast<unsigned long long *>(out_total);
-        return launch_k<uint32_t>(h, p, launch_ops, s);
+        return launch_k<uint32_t>(shape_of(h), p, launch_ops, s);
     } else {
         gh::Params<uint64_t> p = base_params<uint64_t>(h, mode);
         p.in = static_cast<const uint64_t *>(in);
@@ -141,7 +159,7 @@ int launch(gheap_t h, uint32_t mode, const void *in, void *out, uint64_t n,
         p.n_ops = n_ops;
         p.out_counts = out_counts;
         p.out_total = reinterpret_cast<unsigned long long *>(out_total);
-        return launch_k<uint64_t>(h, p, launch_ops, s);
+        return launch_k<uint64_t>(shape_of(h), p, launch_ops, s);
     }
 }
 
@@ -419,6 +437,248 @@ int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k, uint32_t *key_byt
     if (max_nodes) *max_nodes = h->max_nodes;
     if (k) *k = h->k;
     if (key_bytes) *key_bytes = h->key_bytes;
+    return GHEAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// heap sets
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct gheapset_s {
+    int device;
+    uint32_t n;
+    uint32_t k;
+    uint32_t key_bytes;
+    uint32_t flags;
+    uint32_t ipt;
+    uint32_t ctas;
+    int sm_count;
+    uint32_t call_id;
+    gheap_t *heaps;
+    void *d_table;             // gh::HeapView<K>[n]
+    gh::Ctl *d_ctl;
+    unsigned long long *d_stats;
+};
+
+struct gheapset_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+template <typename K>
+int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void *in, void *out,
+               uint32_t *counts, cudaStream_t st)
+{
+    gh::Params<K> p;
+    memset(&p, 0, sizeof(p));
+    p.ctl = S->d_ctl;
+    p.stats = (S->flags & GHEAP_FLAG_STATS) ? S->d_stats : nullptr;
+    p.k = S->k;
+    p.mode = gh::MODE_SET;
+    p.call_id = ++S->call_id;
+    p.timeout_ns = S->heaps[0]->timeout_ns;
+    p.in = static_cast<const K *>(in);
+    p.out = static_cast<K *>(out);
+    p.n_ops = n_ops;
+    p.out_counts = counts;
+    p.table = static_cast<const gh::HeapView<K> *>(S->d_table);
+    p.sops = ops;
+    p.n_heaps = S->n;
+    Shape sp;
+    sp.k = S->k;
+    sp.ipt = S->ipt;
+    sp.ctas = S->ctas;
+    sp.sm_count = S->sm_count;
+    sp.d_ctl = S->d_ctl;
+    return launch_k<K>(sp, p, n_ops, st);
+}
+
+template <typename K>
+void fill_view(gh::HeapView<K> &v, gheap_t h)
+{
+    memset(&v, 0, sizeof(v));
+    v.keys = static_cast<K *>(h->d_keys);
+    v.state = h->d_state;
+    v.buf = static_cast<K *>(h->d_buf);
+    v.hdr = h->d_hdr;
+    v.log = h->d_log;
+    v.log_cap = h->log_cap;
+    v.max_nodes = h->max_nodes;
+}
+
+}  // namespace
+
+extern "C" {
+
+int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities, uint32_t k,
+                   uint32_t key_bytes, uint32_t flags, uint64_t log_capacity)
+{
+    if (!out || !capacities || n_heaps == 0) return GHEAP_ERR_ARG;
+    *out = nullptr;
+    gheapset_t S = (gheapset_t)calloc(1, sizeof(gheapset_s));
+    if (!S) return GHEAP_ERR_OOM;
+    S->heaps = (gheap_t *)calloc(n_heaps, sizeof(gheap_t));
+    if (!S->heaps) { free(S); return GHEAP_ERR_OOM; }
+    S->n = n_heaps;
+    S->k = k;
+    S->key_bytes = key_bytes;
+    S->flags = flags;
+    int rc = GHEAP_OK;
+    for (uint32_t i = 0; i < n_heaps && rc == GHEAP_OK; i++)
+        rc = heap_create(&S->heaps[i], capacities[i], k, key_bytes, 0, log_capacity);
+    if (rc != GHEAP_OK) {
+        heapset_destroy(S);
+        return rc;
+    }
+    S->device = S->heaps[0]->device;
+    S->sm_count = S->heaps[0]->sm_count;
+    S->ipt = S->heaps[0]->ipt;
+    S->ctas = 0;
+    size_t vb = key_bytes == 4 ? sizeof(gh::HeapView<uint32_t>) : sizeof(gh::HeapView<uint64_t>);
+    void *host = calloc(n_heaps, vb);
+    bool ok = host != nullptr &&
+              cudaMalloc(&S->d_table, (size_t)n_heaps * vb) == cudaSuccess &&
+              cudaMalloc((void **)&S->d_ctl, sizeof(gh::Ctl)) == cudaSuccess &&
+              cudaMalloc((void **)&S->d_stats, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
+    if (ok) {
+        for (uint32_t i = 0; i < n_heaps; i++) {
+            if (key_bytes == 4) fill_view(static_cast<gh::HeapView<uint32_t> *>(host)[i], S->heaps[i]);
+            else fill_view(static_cast<gh::HeapView<uint64_t> *>(host)[i], S->heaps[i]);
+        }
+        ok = cudaMemcpy(S->d_table, host, (size_t)n_heaps * vb, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(S->d_stats, 0, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
+    }
+    free(host);
+    if (!ok) {
+        cudaGetLastError();
+        heapset_destroy(S);
+        return GHEAP_ERR_OOM;
+    }
+    *out = S;
+    return GHEAP_OK;
+}
+
+int heapset_destroy(gheapset_t S)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    if (S->heaps) {
+        for (uint32_t i = 0; i < S->n; i++)
+            if (S->heaps[i]) heap_destroy(S->heaps[i]);
+        free(S->heaps);
+    }
+    cudaFree(S->d_table);
+    cudaFree(S->d_ctl);
+    cudaFree(S->d_stats);
+    free(S);
+    return GHEAP_OK;
+}
+
+gheap_t heapset_heap(gheapset_t S, uint32_t i)
+{
+    if (!S || i >= S->n) return nullptr;
+    return S->heaps[i];
+}
+
+int heapset_set_launch(gheapset_t S, uint32_t ctas, uint32_t items_per_thread)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    int rc = heap_set_launch(S->heaps[0], ctas, items_per_thread);
+    if (rc != GHEAP_OK) return rc;
+    S->ctas = ctas;
+    S->ipt = items_per_thread;
+    return GHEAP_OK;
+}
+
+int heapset_set_timeout(gheapset_t S, uint64_t ns)
+{
+    if (!S || ns == 0) return GHEAP_ERR_ARG;
+    for (uint32_t i = 0; i < S->n; i++) heap_set_timeout(S->heaps[i], ns);
+    return GHEAP_OK;
+}
+
+int heapset_ops(gheapset_t S, const gheapset_op *d_ops, uint64_t n_ops, const void *d_in_keys,
+                void *d_out_keys, uint32_t *d_out_counts, void *stream)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    if (n_ops == 0) return GHEAP_OK;
+    if (!d_ops) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (S->key_bytes == 4)
+        return set_launch<uint32_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts,
+                                    (cudaStream_t)stream);
+    return set_launch<uint64_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts,
+                                (cudaStream_t)stream);
+}
+
+int heapset_sync(gheapset_t S)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    int first = GHEAP_OK;
+    for (uint32_t i = 0; i < S->n; i++) {
+        int rc = heap_sync(S->heaps[i]);
+        if (rc != GHEAP_OK && first == GHEAP_OK) first = rc;
+    }
+    return first;
+}
+
+int heapset_reset(gheapset_t S, void *stream)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    for (uint32_t i = 0; i < S->n; i++) {
+        int rc = heap_reset(S->heaps[i], stream);
+        if (rc != GHEAP_OK) return rc;
+    }
+    return cuda_err(cudaMemsetAsync(S->d_stats, 0, gh::N_STATS * sizeof(unsigned long long),
+                                    (cudaStream_t)stream));
+}
+
+int heapset_graph_create(gheapset_t S, const gheapset_op *d_ops, uint64_t n_ops,
+                         const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
+                         gheapset_graph_t *out)
+{
+    if (!S || !out) return GHEAP_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return GHEAP_ERR_CUDA;
+    gheapset_graph_t G = (gheapset_graph_t)calloc(1, sizeof(gheapset_graph_s));
+    if (!G) { cudaStreamDestroy(cs); return GHEAP_ERR_OOM; }
+    int rc = GHEAP_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = GHEAP_ERR_CUDA;
+    if (rc == GHEAP_OK) {
+        rc = heapset_ops(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (rc == GHEAP_OK && e != cudaSuccess) rc = GHEAP_ERR_CUDA;
+        G->graph = g;
+        if (rc == GHEAP_OK && cudaGraphInstantiate(&G->exec, g, 0) != cudaSuccess) rc = GHEAP_ERR_CUDA;
+    }
+    cudaStreamDestroy(cs);
+    if (rc != GHEAP_OK) {
+        cudaGetLastError();
+        heapset_graph_destroy(G);
+        return rc;
+    }
+    *out = G;
+    return GHEAP_OK;
+}
+
+int heapset_graph_launch(gheapset_graph_t G, void *stream)
+{
+    if (!G || !G->exec) return GHEAP_ERR_ARG;
+    return cuda_err(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+}
+
+int heapset_graph_destroy(gheapset_graph_t G)
+{
+    if (!G) return GHEAP_ERR_ARG;
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    free(G);
     return GHEAP_OK;
 }
 

@@ -55,7 +55,7 @@ enum : uint32_t {
 constexpr uint32_t ST_GAVE_UP = ~0u;
 constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
-enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2 };
+enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2, MODE_SET = 3 };
 
 enum : uint32_t { E_NONE = 0, E_TIMEOUT = 1, E_FULL = 2, E_STATE = 3 };
 
@@ -140,8 +140,11 @@ struct Params {
     unsigned long long n;        // MODE_INSERT: keys; MODE_DELETE: keys wanted
     const gheap_op *ops;         // MODE_OPS
     unsigned long long n_ops;
-    uint32_t *out_counts;        // MODE_OPS, may be nullptr
+    uint32_t *out_counts;        // MODE_OPS / MODE_SET, may be nullptr
     unsigned long long *out_total;  // MODE_DELETE, may be nullptr
+    const HeapView<K> *table;    // MODE_SET: one view per heap
+    const gheapset_op *sops;     // MODE_SET operations
+    uint32_t n_heaps;            // MODE_SET
 };
 
 // Block-shared scalars that carry decisions between the control warp and the
@@ -1402,21 +1405,40 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared sh;
+    __shared__ HeapView<K> set_view;   // MODE_SET: the heap of the current op
+    __shared__ uint32_t set_kind, set_n, set_skip;
+    __shared__ unsigned long long set_off;
     const uint32_t k = p.k;
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
-    const HeapView<K> &H = p.h;
+    const bool multi = p.mode == MODE_SET;
+    const HeapView<K> &H = multi ? set_view : p.h;
     if (threadIdx.x < N_STATS) sh.cnt[threadIdx.x] = 0;
 
     unsigned long long n_ops;
-    if (p.mode == MODE_OPS) n_ops = p.n_ops;
+    if (p.mode == MODE_OPS || multi) n_ops = p.n_ops;
     else n_ops = (p.n + k - 1) / k;
 
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned long long op = atomicAdd(&p.ctl->next_op, 1ull);
             sh.op = op;
-            int stop = op >= n_ops || ld_relaxed(&H.hdr->err) != E_NONE;
-            if (!stop && p.mode == MODE_DELETE && ld_relaxed(&p.ctl->drained)) stop = 1;
+            int stop = op >= n_ops;
+            if (!stop && multi) {
+                // the op names its heap; a heap with a sticky error skips it
+                const gheapset_op d = p.sops[op];
+                const uint32_t hid = d.heap < p.n_heaps ? d.heap : 0u;
+                set_view = p.table[hid];
+                set_kind = d.kind_n >> 24;
+                set_n = d.kind_n & 0xFFFFFFu;
+                set_off = d.offset;
+                set_skip = d.heap >= p.n_heaps || set_n > k ||
+                           ld_relaxed(&set_view.hdr->err) != E_NONE;
+                // a malformed op is the named heap's sticky error
+                if (d.heap < p.n_heaps && set_n > k) set_err(set_view, E_STATE);
+            } else if (!stop) {
+                stop = ld_relaxed(&H.hdr->err) != E_NONE;
+                if (!stop && p.mode == MODE_DELETE && ld_relaxed(&p.ctl->drained)) stop = 1;
+            }
             sh.stop = stop;
             sh.abort = 0;
             sh.halt = 0;
@@ -1435,12 +1457,22 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
             kind = GHEAP_OP_DEL;
             n = k;
             off = 0;
+        } else if (multi) {
+            if (set_skip) {
+                if (threadIdx.x == 0 && p.out_counts) p.out_counts[op] = 0;
+                bar_all();
+                continue;
+            }
+            kind = set_kind;
+            n = set_n;
+            off = set_off;
         } else {
             gheap_op d = p.ops[op];
             kind = d.kind;
             n = d.n;
             off = d.offset;
         }
+        const bool listed = p.mode == MODE_OPS || multi;
         if (kind == GHEAP_OP_INS) {
             // stage and sort the batch before taking the root (Section 4.1)
             if (!is_ctrl()) {
@@ -1459,17 +1491,19 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
                 if (threadIdx.x == 0) lap(sh, STAT_INS_SORT_CYC, ts);
             }
             bar_all();
-            ok = ins_op<K, IPT>(p, H, sh, base, n, p.mode == MODE_OPS ? op : off);
+            ok = ins_op<K, IPT>(p, H, sh, base, n, listed ? op : off);
             if (threadIdx.x == 0) {
                 stat_add(sh, STAT_INS, 1);
-                if (p.mode == MODE_OPS && p.out_counts) p.out_counts[op] = n;
+                if (listed && p.out_counts) p.out_counts[op] = ok ? n : 0u;
             }
         } else {
             ok = del_op<K, IPT>(p, H, sh, base, n, off, op,
-                                p.mode == MODE_OPS && p.out_counts ? p.out_counts + op : nullptr);
+                                listed && p.out_counts ? p.out_counts + op : nullptr);
             if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
         }
-        if (!ok) break;
+        // one heap giving up ends a single-heap launch; in a set the other
+        // heaps go on (the failed heap's later ops are skipped)
+        if (!ok && !multi) break;
         bar_all();
     }
     bar_all();

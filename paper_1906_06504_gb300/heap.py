@@ -17,8 +17,9 @@ ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -
 FLAG_STATS = 1
 OP_INS, OP_DEL = 1, 2
 
-# gheap_op and gheap_log_entry of include/gheap.h
+# gheap_op, gheapset_op and gheap_log_entry of include/gheap.h
 OP_DTYPE = np.dtype([("kind", "<u4"), ("n", "<u4"), ("offset", "<u8")])
+SETOP_DTYPE = np.dtype([("heap", "<u4"), ("kind_n", "<u4"), ("offset", "<u8")])
 LOG_DTYPE = np.dtype([("call_id", "<u4"), ("kind_n", "<u4"), ("ref", "<u8")])
 STAT_NAMES = ("node_loads", "node_stores", "merges", "merges_skipped", "ins_ops",
               "del_ops", "lock_waits", "root_hold_ns",
@@ -63,6 +64,17 @@ def lib():
             "heap_slot_to_node": (u64, [u64]),
             "heap_get_stats": (ctypes.c_int, [vp, u64p, u32]),
             "heap_debug_hold_root": (ctypes.c_int, [vp, vp]),
+            "heapset_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64p, u32, u32, u32, u64]),
+            "heapset_destroy": (ctypes.c_int, [vp]),
+            "heapset_heap": (vp, [vp, u32]),
+            "heapset_set_launch": (ctypes.c_int, [vp, u32, u32]),
+            "heapset_set_timeout": (ctypes.c_int, [vp, u64]),
+            "heapset_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, vp]),
+            "heapset_sync": (ctypes.c_int, [vp]),
+            "heapset_reset": (ctypes.c_int, [vp, vp]),
+            "heapset_graph_create": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, ctypes.POINTER(vp)]),
+            "heapset_graph_launch": (ctypes.c_int, [vp, vp]),
+            "heapset_graph_destroy": (ctypes.c_int, [vp]),
             "heap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -92,17 +104,24 @@ def slot_to_node(j):
 class GHeap:
     """A generalized concurrent heap in device memory (include/gheap.h)."""
 
-    def __init__(self, capacity, k=1024, key_bytes=4, log_capacity=0, stats=False):
+    def __init__(self, capacity, k=1024, key_bytes=4, log_capacity=0, stats=False, _handle=None):
         L = lib()
-        h = ctypes.c_void_p()
-        _check(L.heap_create(ctypes.byref(h), int(capacity), int(k), int(key_bytes),
-                             FLAG_STATS if stats else 0, int(log_capacity)), "heap_create")
+        self._owned = _handle is None
+        if _handle is None:
+            h = ctypes.c_void_p()
+            _check(L.heap_create(ctypes.byref(h), int(capacity), int(k), int(key_bytes),
+                                 FLAG_STATS if stats else 0, int(log_capacity)), "heap_create")
+        else:
+            h = ctypes.c_void_p(_handle)
         self._h = h
-        self.k = int(k)
-        self.key_bytes = int(key_bytes)
-        self.capacity = int(capacity)
         mn = ctypes.c_uint64()
-        _check(L.heap_geometry(h, ctypes.byref(mn), None, None), "heap_geometry")
+        kk = ctypes.c_uint32()
+        kb = ctypes.c_uint32()
+        _check(L.heap_geometry(h, ctypes.byref(mn), ctypes.byref(kk), ctypes.byref(kb)),
+               "heap_geometry")
+        self.k = int(kk.value)
+        self.key_bytes = int(kb.value)
+        self.capacity = int(capacity)
         self.max_nodes = int(mn.value)
 
     # -- configuration
@@ -211,7 +230,8 @@ class GHeap:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().heap_destroy(self._h)
+            if self._owned:
+                lib().heap_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -225,3 +245,93 @@ class GHeap:
 
     def __exit__(self, *a):
         self.close()
+
+
+class GHeapSet:
+    """Many independent heaps driven by one persistent launch (include/gheap.h
+    heap sets).  `heaps[i]` is a non-owning GHeap view of heap i."""
+
+    def __init__(self, capacities, k=1024, key_bytes=4, log_capacity=0, stats=False):
+        L = lib()
+        caps = (ctypes.c_uint64 * len(capacities))(*[int(c) for c in capacities])
+        h = ctypes.c_void_p()
+        _check(L.heapset_create(ctypes.byref(h), len(capacities), caps, int(k), int(key_bytes),
+                                FLAG_STATS if stats else 0, int(log_capacity)), "heapset_create")
+        self._s = h
+        self.k = int(k)
+        self.key_bytes = int(key_bytes)
+        self.heaps = [GHeap(c, _handle=L.heapset_heap(h, i)) for i, c in enumerate(capacities)]
+
+    def set_launch(self, ctas=0, items_per_thread=8):
+        _check(lib().heapset_set_launch(self._s, int(ctas), int(items_per_thread)),
+               "heapset_set_launch")
+
+    def set_timeout(self, ns):
+        _check(lib().heapset_set_timeout(self._s, int(ns)), "heapset_set_timeout")
+
+    def _ptrs(self, ops_dev, in_keys, out_keys, counts):
+        n_ops = ops_dev.numel() * ops_dev.element_size() // SETOP_DTYPE.itemsize
+        return (n_ops, ctypes.c_void_p(ops_dev.data_ptr()),
+                ctypes.c_void_p(in_keys.data_ptr() if in_keys is not None else 0),
+                ctypes.c_void_p(out_keys.data_ptr() if out_keys is not None else 0),
+                ctypes.c_void_p(counts.data_ptr() if counts is not None else 0))
+
+    def ops(self, ops_dev, in_keys, out_keys, counts=None, stream=None):
+        n_ops, o, i, ou, c = self._ptrs(ops_dev, in_keys, out_keys, counts)
+        _check(lib().heapset_ops(self._s, o, n_ops, i, ou, c, _stream_ptr(stream)), "heapset_ops")
+
+    def graph(self, ops_dev, in_keys, out_keys, counts=None):
+        """A captured CUDA graph of ops(); launch() replays it."""
+        n_ops, o, i, ou, c = self._ptrs(ops_dev, in_keys, out_keys, counts)
+        g = ctypes.c_void_p()
+        _check(lib().heapset_graph_create(self._s, o, n_ops, i, ou, c, ctypes.byref(g)),
+               "heapset_graph_create")
+        return SetGraph(g, (ops_dev, in_keys, out_keys, counts))
+
+    def sync(self):
+        _check(lib().heapset_sync(self._s), "heapset_sync")
+
+    def sync_code(self):
+        return int(lib().heapset_sync(self._s))
+
+    def reset(self, stream=None):
+        _check(lib().heapset_reset(self._s, _stream_ptr(stream)), "heapset_reset")
+
+    def close(self):
+        if getattr(self, "_s", None):
+            for h in self.heaps:
+                h._h = None
+            lib().heapset_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class SetGraph:
+    def __init__(self, g, keep):
+        self._g = g
+        self._keep = keep   # the captured arrays must outlive the graph
+
+    def launch(self, stream=None):
+        _check(lib().heapset_graph_launch(self._g, _stream_ptr(stream)), "heapset_graph_launch")
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lib().heapset_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -149,3 +149,24 @@ def poisson_arrivals(seed, n, rate_per_s):
     x = splitmix64(seed, n)
     u = ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / (1 << 53))
     return np.cumsum(-np.log(u) / rate_per_s)
+
+
+def set_phase_ops(sizes, k, kind, base_offsets=None):
+    """Operation list of one phase over many heaps: heap h gets ceil(sizes[h]/k)
+    ops of `kind` (1 = INS, 2 = DEL) over its own slice [base_offsets[h],
+    base_offsets[h] + sizes[h]) of the launch's key array, the last one partial.
+    Ops are interleaved round-robin across heaps so that every heap has work
+    from the start.  Returns a structured array (heap, kind_n, offset)."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    if base_offsets is None:
+        base_offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    counts = -(-sizes // k)
+    heap = np.repeat(np.arange(sizes.size, dtype=np.int64), counts)
+    j = np.arange(heap.size) - np.repeat(np.cumsum(counts) - counts, counts)
+    n = np.minimum(k, sizes[heap] - j * k)
+    order = np.lexsort((heap, j))      # round j of every heap, then j + 1, ...
+    ops = np.zeros(heap.size, dtype=[("heap", "<u4"), ("kind_n", "<u4"), ("offset", "<u8")])
+    ops["heap"] = heap[order]
+    ops["kind_n"] = (int(kind) << 24) | n[order]
+    ops["offset"] = (np.asarray(base_offsets)[heap] + j * k)[order]
+    return ops

@@ -1,0 +1,204 @@
+"""Parity of heap sets (many heaps, one persistent launch) with the CPU oracle.
+
+Every heap of a set keeps its own linearization record; replaying each one
+through the oracle must reproduce every DEL output of that heap bit for bit,
+whatever the other heaps did in the same launch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1906_06504_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_06504_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+from heaputil import check_properties, np_dtype, to_dev, to_host  # noqa: E402
+
+OP_INS, OP_DEL = 1, 2
+
+
+def GHeapSet(*a, **kw):
+    from paper_1906_06504_gb300.heap import GHeapSet as G
+    return G(*a, **kw)
+
+
+class SetRun:
+    """Launches op lists on a set and replays each heap's record."""
+
+    def __init__(self, hs):
+        self.hs = hs
+        self.launches = {}
+        self.next_id = 1
+        self.kb = hs.key_bytes
+
+    def launch(self, ops, in_keys, out_size):
+        dt = np_dtype(self.kb)
+        ops = np.ascontiguousarray(ops)
+        in_keys = np.ascontiguousarray(in_keys, dtype=dt)
+        ops_dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        out = torch.zeros(max(out_size, 1), dtype=torch.int32 if self.kb == 4 else torch.int64,
+                          device="cuda")
+        counts = torch.zeros(len(ops), dtype=torch.int32, device="cuda")
+        self.hs.ops(ops_dev, to_dev(in_keys) if in_keys.size else None, out, counts)
+        self.launches[self.next_id] = (ops, in_keys, out, counts)
+        self.next_id += 1
+        return out, counts
+
+    def replay(self):
+        self.hs.sync()
+        dt = np_dtype(self.kb)
+        host = {cid: (to_host(o, self.kb), c.cpu().numpy())
+                for cid, (_, _, o, c) in self.launches.items()}
+        checked = 0
+        for hid, h in enumerate(self.hs.heaps):
+            log, total = h.log()
+            assert log.size == total
+            q = oracle.BinaryHeapPQ()
+            try:
+                for e in log:
+                    ops, ins, _, _ = self.launches[int(e["call_id"])]
+                    ref = int(e["ref"])
+                    kind = int(e["kind_n"]) >> 24
+                    n = int(e["kind_n"]) & 0xFFFFFF
+                    op = ops[ref]
+                    assert int(op["heap"]) == hid
+                    assert (int(op["kind_n"]) >> 24) == kind
+                    off = int(op["offset"])
+                    want_n = int(op["kind_n"]) & 0xFFFFFF
+                    if kind == OP_INS:
+                        assert n == want_n
+                        q.push(ins[off:off + n])
+                    else:
+                        out, cnt = host[int(e["call_id"])]
+                        assert n == min(want_n, len(q)) == int(cnt[ref])
+                        want = q.pop(n, dtype=dt)
+                        assert np.array_equal(out[off:off + n], want), (hid, ref)
+                        checked += 1
+                assert len(q) == h.size()
+            finally:
+                q.close()
+        return checked
+
+
+def random_set_ops(rng, n_heaps, k, n_ops, key_bytes, prefill=0):
+    dt = np_dtype(key_bytes)
+    heap = rng.integers(0, n_heaps, n_ops)
+    kind = np.where(rng.random(n_ops) < 0.55, OP_INS, OP_DEL)
+    n = rng.integers(1, k + 1, n_ops)
+    n[:prefill] = k
+    kind[:prefill] = OP_INS
+    ops = np.zeros(n_ops, dtype=[("heap", "<u4"), ("kind_n", "<u4"), ("offset", "<u8")])
+    ops["heap"] = heap
+    ops["kind_n"] = (kind.astype(np.int64) << 24) | n
+    ins = kind == OP_INS
+    in_off = np.zeros(n_ops, dtype=np.int64)
+    in_off[ins] = np.concatenate([[0], np.cumsum(n[ins])[:-1]])
+    out_off = np.zeros(n_ops, dtype=np.int64)
+    out_off[~ins] = np.concatenate([[0], np.cumsum(n[~ins])[:-1]]) if (~ins).any() else []
+    ops["offset"] = np.where(ins, in_off, out_off)
+    keys = rng.integers(0, np.iinfo(dt).max, int(n[ins].sum()), dtype=dt, endpoint=True)
+    return ops, keys, int(n[~ins].sum())
+
+
+@pytest.mark.parametrize("k,key_bytes", [(64, 4), (1024, 4), (256, 8)])
+def test_heapset_random_ops_replay(k, key_bytes):
+    rng = np.random.default_rng(31 + k + key_bytes)
+    n_heaps = 12
+    caps = [int(c) for c in rng.integers(200 * k, 300 * k, n_heaps)]
+    n_ops = 3000 if k <= 256 else 1200
+    with GHeapSet(caps, k=k, key_bytes=key_bytes, log_capacity=n_ops + 64) as hs:
+        run = SetRun(hs)
+        ops, keys, out_size = random_set_ops(rng, n_heaps, k, n_ops, key_bytes, prefill=n_heaps * 4)
+        run.launch(ops, keys, out_size)
+        # a second launch on the same heaps continues from their state
+        ops2, keys2, out2 = random_set_ops(rng, n_heaps, k, n_ops // 2, key_bytes)
+        run.launch(ops2, keys2, out2)
+        assert run.replay() > 0
+        for h in hs.heaps:
+            check_properties(h)
+
+
+def test_heapset_phased_loguniform_sizes():
+    """Insert-all then delete-all on 48 heaps with log-uniform sizes; in each
+    heap's root order the DEL outputs concatenate to its sorted input."""
+    k = 256
+    sizes = inputs.loguniform_sizes(inputs.config_seed(5), 48, 8, 15)
+    total = int(sizes.sum())
+    keys = inputs.keys_u32(inputs.config_seed(5), total)
+    with GHeapSet([int(s) for s in sizes], k=k, log_capacity=int(-(-sizes.max() // k)) * 2 + 8) as hs:
+        run = SetRun(hs)
+        run.launch(inputs.set_phase_ops(sizes, k, OP_INS), keys, 0)
+        dops = inputs.set_phase_ops(sizes, k, OP_DEL)
+        out, counts = run.launch(dops, np.empty(0, np.uint32), total)
+        run.replay()
+        hs.sync()
+        got = to_host(out, 4)
+        base = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        for hid in range(sizes.size):
+            seg = got[base[hid]:base[hid] + sizes[hid]]
+            # the ops of one heap may take the root in any order, so check the
+            # multiset and that each batch is ascending
+            mine = keys[base[hid]:base[hid] + sizes[hid]]
+            assert np.array_equal(np.sort(seg), np.sort(mine))
+            assert hs.heaps[hid].size() == 0
+
+
+def test_heapset_graph_replay_matches_direct():
+    """A captured launch replayed twice (with a reset between) gives the same
+    per-heap contents as the direct launch."""
+    k = 128
+    sizes = np.array([1000, 5000, 128, 70, 20000, 3333])
+    keys = inputs.keys_u32(77, int(sizes.sum()))
+    ins = inputs.set_phase_ops(sizes, k, OP_INS)
+    with GHeapSet([int(s) for s in sizes], k=k) as hs:
+        ops_dev = torch.from_numpy(ins.view(np.uint8).copy()).cuda()
+        kd = to_dev(keys)
+        g = hs.graph(ops_dev, kd, None)
+        snaps = []
+        for _ in range(2):
+            hs.reset()
+            g.launch()
+            hs.sync()
+            snaps.append([h.snapshot() for h in hs.heaps])
+        g.close()
+        hs.reset()
+        hs.ops(ops_dev, kd, None)
+        hs.sync()
+        direct = [h.snapshot() for h in hs.heaps]
+        for s0, s1, d in zip(snaps[0], snaps[1], direct):
+            # same multiset per heap and same node count, whatever the order
+            for s in (s0, s1):
+                assert s[3][:2] == d[3][:2]
+                m = d[3][0]
+                a = np.sort(np.concatenate([s[0][1:m + 1].ravel(), s[2][:s[3][1]]]))
+                b = np.sort(np.concatenate([d[0][1:m + 1].ravel(), d[2][:d[3][1]]]))
+                assert np.array_equal(a, b)
+
+
+def test_heapset_error_is_per_heap():
+    """A heap whose root lock never frees times out; the other heaps of the
+    same launch finish correctly."""
+    k = 64
+    sizes = np.array([4096, 4096, 4096])
+    keys = inputs.keys_u32(9, int(sizes.sum()))
+    with GHeapSet([int(s) for s in sizes], k=k, log_capacity=256) as hs:
+        hs.set_timeout(50_000_000)
+        hs.heaps[1].debug_hold_root()
+        run = SetRun(hs)
+        run.launch(inputs.set_phase_ops(sizes, k, OP_INS), keys, 0)
+        assert hs.sync_code() == -4
+        assert hs.heaps[0].size() == 4096 and hs.heaps[2].size() == 4096
+        check_properties(hs.heaps[0])
+        check_properties(hs.heaps[2])
