@@ -185,26 +185,43 @@ int heap_debug_hold_root(gheap_t h, void *stream);
 typedef struct gheapset_s *gheapset_t;
 
 /* One operation of heapset_ops: heap index, kind_n = (GHEAP_OP_INS or
- * GHEAP_OP_DEL) << 24 | n (1..k), and the key offset into the launch's
- * input (INS) or output (DEL) array. */
+ * GHEAP_OP_DEL) << 24 | flags | n (1..k), and the key offset into the
+ * launch's input (INS) or output (DEL) array.  With GHEAPSET_CURSOR (DEL
+ * only), `offset` is instead a request index r: the op writes its keys at
+ * d_req_base[r] + d_req_cursor[r] and advances d_req_cursor[r] by its count
+ * while it holds the heap's root, so that the DELs of one request fill one
+ * contiguous ascending result whatever order they run in. */
 typedef struct {
     uint32_t heap;
     uint32_t kind_n;
     uint64_t offset;
 } gheapset_op;
 
-/* Creates n_heaps empty heaps; capacities[i] (host array) is heap i's
- * capacity in keys.  k, key_bytes, flags and log_capacity (per heap) as for
- * heap_create.  All heaps live on the current device. */
+#define GHEAPSET_CURSOR (1u << 23)
+
+/* Creates a set of n_heaps slots; capacities[i] (host array) is heap i's
+ * capacity in keys, 0 for an empty slot (see heapset_bind).  k, key_bytes,
+ * flags and log_capacity (per heap) as for heap_create.  All heaps live on
+ * the current device. */
 int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities, uint32_t k,
                    uint32_t key_bytes, uint32_t flags, uint64_t log_capacity);
 
 /* Frees every heap of the set (synchronizes the device first). */
 int heapset_destroy(gheapset_t s);
 
-/* Heap i of the set, for the single-heap queries (heap_size, heap_get_log,
- * heap_snapshot, heap_get_stats, heap_reset).  Owned by the set. */
+/* Heap i of the set (NULL for an empty slot), for the single-heap calls
+ * (heap_size, heap_get_log, heap_snapshot, heap_reset, ...). */
 gheap_t heapset_heap(gheapset_t s, uint32_t i);
+
+/* Puts heap h (created by heap_create with the set's k and key_bytes, owned
+ * by the caller) into empty slot i, enqueued on `stream`; later launches on
+ * that stream see it.  Errors: ARG (slot taken, shape mismatch). */
+int heapset_bind(gheapset_t s, uint32_t i, gheap_t h, void *stream);
+
+/* Empties slot i (enqueued on `stream`); ops naming it are skipped.  A heap
+ * the set created is destroyed after the device is synchronized; a bound
+ * heap goes back to its owner. */
+int heapset_unbind(gheapset_t s, uint32_t i, void *stream);
 
 /* Launch shape and wait bound, as heap_set_launch / heap_set_timeout. */
 int heapset_set_launch(gheapset_t s, uint32_t ctas, uint32_t items_per_thread);
@@ -218,6 +235,13 @@ int heapset_set_timeout(gheapset_t s, uint64_t ns);
  * GHEAP_ERR_FULL.  Capacities are not checked on the host. */
 int heapset_ops(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops, const void *d_in_keys,
                 void *d_out_keys, uint32_t *d_out_counts, void *stream);
+
+/* heapset_ops with per-request cursors for GHEAPSET_CURSOR DELs: device
+ * uint64_t arrays indexed by request (d_req_cursor is read and advanced; the
+ * caller zeroes it). */
+int heapset_ops_req(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops,
+                    const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
+                    const uint64_t *d_req_base, uint64_t *d_req_cursor, void *stream);
 
 /* Waits for the device and returns the first sticky error of any heap. */
 int heapset_sync(gheapset_t s);

@@ -456,7 +456,9 @@ struct gheapset_s {
     uint32_t ctas;
     int sm_count;
     uint32_t call_id;
-    gheap_t *heaps;
+    uint64_t timeout_ns;
+    gheap_t *heaps;            // NULL for an empty slot
+    uint8_t *owned;            // heaps[i] was created by the set
     void *d_table;             // gh::HeapView<K>[n]
     gh::Ctl *d_ctl;
     unsigned long long *d_stats;
@@ -471,7 +473,7 @@ namespace {
 
 template <typename K>
 int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void *in, void *out,
-               uint32_t *counts, cudaStream_t st)
+               uint32_t *counts, const uint64_t *req_base, uint64_t *req_cursor, cudaStream_t st)
 {
     gh::Params<K> p;
     memset(&p, 0, sizeof(p));
@@ -480,7 +482,7 @@ int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void 
     p.k = S->k;
     p.mode = gh::MODE_SET;
     p.call_id = ++S->call_id;
-    p.timeout_ns = S->heaps[0]->timeout_ns;
+    p.timeout_ns = S->timeout_ns;
     p.in = static_cast<const K *>(in);
     p.out = static_cast<K *>(out);
     p.n_ops = n_ops;
@@ -488,6 +490,8 @@ int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void 
     p.table = static_cast<const gh::HeapView<K> *>(S->d_table);
     p.sops = ops;
     p.n_heaps = S->n;
+    p.req_base = reinterpret_cast<const unsigned long long *>(req_base);
+    p.req_cursor = reinterpret_cast<unsigned long long *>(req_cursor);
     Shape sp;
     sp.k = S->k;
     sp.ipt = S->ipt;
@@ -522,21 +526,35 @@ int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities
     gheapset_t S = (gheapset_t)calloc(1, sizeof(gheapset_s));
     if (!S) return GHEAP_ERR_OOM;
     S->heaps = (gheap_t *)calloc(n_heaps, sizeof(gheap_t));
-    if (!S->heaps) { free(S); return GHEAP_ERR_OOM; }
+    S->owned = (uint8_t *)calloc(n_heaps, 1);
+    if (!S->heaps || !S->owned) { free(S->heaps); free(S->owned); free(S); return GHEAP_ERR_OOM; }
     S->n = n_heaps;
     S->k = k;
     S->key_bytes = key_bytes;
     S->flags = flags;
+    S->timeout_ns = 2000000000ull;
+    if (k < 1 || k > 2048 || (k & (k - 1)) != 0 || (key_bytes != 4 && key_bytes != 8)) {
+        heapset_destroy(S);
+        return GHEAP_ERR_ARG;
+    }
     int rc = GHEAP_OK;
-    for (uint32_t i = 0; i < n_heaps && rc == GHEAP_OK; i++)
+    for (uint32_t i = 0; i < n_heaps && rc == GHEAP_OK; i++) {
+        if (capacities[i] == 0) continue;
         rc = heap_create(&S->heaps[i], capacities[i], k, key_bytes, 0, log_capacity);
+        S->owned[i] = rc == GHEAP_OK;
+    }
     if (rc != GHEAP_OK) {
         heapset_destroy(S);
         return rc;
     }
-    S->device = S->heaps[0]->device;
-    S->sm_count = S->heaps[0]->sm_count;
-    S->ipt = S->heaps[0]->ipt;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&S->device) != cudaSuccess ||
+        cudaGetDeviceProperties(&prop, S->device) != cudaSuccess) {
+        heapset_destroy(S);
+        return GHEAP_ERR_CUDA;
+    }
+    S->sm_count = prop.multiProcessorCount;
+    S->ipt = k >= 2048 ? 16 : 8;
     S->ctas = 0;
     size_t vb = key_bytes == 4 ? sizeof(gh::HeapView<uint32_t>) : sizeof(gh::HeapView<uint64_t>);
     void *host = calloc(n_heaps, vb);
@@ -546,6 +564,7 @@ int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities
               cudaMalloc((void **)&S->d_stats, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
     if (ok) {
         for (uint32_t i = 0; i < n_heaps; i++) {
+            if (!S->heaps[i]) continue;   // calloc left the view zero: empty slot
             if (key_bytes == 4) fill_view(static_cast<gh::HeapView<uint32_t> *>(host)[i], S->heaps[i]);
             else fill_view(static_cast<gh::HeapView<uint64_t> *>(host)[i], S->heaps[i]);
         }
@@ -567,9 +586,10 @@ int heapset_destroy(gheapset_t S)
     if (!S) return GHEAP_ERR_ARG;
     if (S->heaps) {
         for (uint32_t i = 0; i < S->n; i++)
-            if (S->heaps[i]) heap_destroy(S->heaps[i]);
+            if (S->heaps[i] && S->owned && S->owned[i]) heap_destroy(S->heaps[i]);
         free(S->heaps);
     }
+    free(S->owned);
     cudaFree(S->d_table);
     cudaFree(S->d_ctl);
     cudaFree(S->d_stats);
@@ -586,8 +606,10 @@ gheap_t heapset_heap(gheapset_t S, uint32_t i)
 int heapset_set_launch(gheapset_t S, uint32_t ctas, uint32_t items_per_thread)
 {
     if (!S) return GHEAP_ERR_ARG;
-    int rc = heap_set_launch(S->heaps[0], ctas, items_per_thread);
-    if (rc != GHEAP_OK) return rc;
+    if (items_per_thread != 4 && items_per_thread != 8 && items_per_thread != 16)
+        return GHEAP_ERR_ARG;
+    if (merge_threads_for(S->k, items_per_thread) > max_merge_threads(items_per_thread))
+        return GHEAP_ERR_ARG;
     S->ctas = ctas;
     S->ipt = items_per_thread;
     return GHEAP_OK;
@@ -596,7 +618,49 @@ int heapset_set_launch(gheapset_t S, uint32_t ctas, uint32_t items_per_thread)
 int heapset_set_timeout(gheapset_t S, uint64_t ns)
 {
     if (!S || ns == 0) return GHEAP_ERR_ARG;
-    for (uint32_t i = 0; i < S->n; i++) heap_set_timeout(S->heaps[i], ns);
+    S->timeout_ns = ns;
+    for (uint32_t i = 0; i < S->n; i++)
+        if (S->heaps[i]) heap_set_timeout(S->heaps[i], ns);
+    return GHEAP_OK;
+}
+
+int heapset_bind(gheapset_t S, uint32_t i, gheap_t h, void *stream)
+{
+    if (!S || !h || i >= S->n || S->heaps[i]) return GHEAP_ERR_ARG;
+    if (h->k != S->k || h->key_bytes != S->key_bytes) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    cudaError_t e;
+    if (S->key_bytes == 4) {
+        gh::HeapView<uint32_t> v;
+        fill_view(v, h);
+        e = cudaMemcpyAsync(static_cast<gh::HeapView<uint32_t> *>(S->d_table) + i, &v, sizeof(v),
+                            cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    } else {
+        gh::HeapView<uint64_t> v;
+        fill_view(v, h);
+        e = cudaMemcpyAsync(static_cast<gh::HeapView<uint64_t> *>(S->d_table) + i, &v, sizeof(v),
+                            cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    }
+    // the view lives on this stack frame: wait for the copy before returning
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    h->timeout_ns = S->timeout_ns;
+    S->heaps[i] = h;
+    S->owned[i] = 0;
+    return GHEAP_OK;
+}
+
+int heapset_unbind(gheapset_t S, uint32_t i, void *stream)
+{
+    if (!S || i >= S->n || !S->heaps[i]) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    size_t vb = S->key_bytes == 4 ? sizeof(gh::HeapView<uint32_t>) : sizeof(gh::HeapView<uint64_t>);
+    cudaError_t e = cudaMemsetAsync(static_cast<char *>(S->d_table) + (size_t)i * vb, 0, vb,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (S->owned[i]) heap_destroy(S->heaps[i]);   // synchronizes the device first
+    S->heaps[i] = nullptr;
+    S->owned[i] = 0;
     return GHEAP_OK;
 }
 
@@ -609,16 +673,34 @@ int heapset_ops(gheapset_t S, const gheapset_op *d_ops, uint64_t n_ops, const vo
     if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
     if (S->key_bytes == 4)
         return set_launch<uint32_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts,
-                                    (cudaStream_t)stream);
+                                    nullptr, nullptr, (cudaStream_t)stream);
+    return set_launch<uint64_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts, nullptr,
+                                nullptr, (cudaStream_t)stream);
+}
+
+int heapset_ops_req(gheapset_t S, const gheapset_op *d_ops, uint64_t n_ops,
+                    const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
+                    const uint64_t *d_req_base, uint64_t *d_req_cursor, void *stream)
+{
+    if (!S) return GHEAP_ERR_ARG;
+    if (n_ops == 0) return GHEAP_OK;
+    if (!d_ops) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (S->key_bytes == 4)
+        return set_launch<uint32_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts,
+                                    d_req_base, d_req_cursor, (cudaStream_t)stream);
     return set_launch<uint64_t>(S, d_ops, n_ops, d_in_keys, d_out_keys, d_out_counts,
-                                (cudaStream_t)stream);
+                                d_req_base, d_req_cursor, (cudaStream_t)stream);
 }
 
 int heapset_sync(gheapset_t S)
 {
     if (!S) return GHEAP_ERR_ARG;
     int first = GHEAP_OK;
+    if (cudaSetDevice(S->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return GHEAP_ERR_CUDA;
     for (uint32_t i = 0; i < S->n; i++) {
+        if (!S->heaps[i]) continue;
         int rc = heap_sync(S->heaps[i]);
         if (rc != GHEAP_OK && first == GHEAP_OK) first = rc;
     }
@@ -629,6 +711,7 @@ int heapset_reset(gheapset_t S, void *stream)
 {
     if (!S) return GHEAP_ERR_ARG;
     for (uint32_t i = 0; i < S->n; i++) {
+        if (!S->heaps[i]) continue;
         int rc = heap_reset(S->heaps[i], stream);
         if (rc != GHEAP_OK) return rc;
     }

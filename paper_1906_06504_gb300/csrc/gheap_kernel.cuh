@@ -145,6 +145,8 @@ struct Params {
     const HeapView<K> *table;    // MODE_SET: one view per heap
     const gheapset_op *sops;     // MODE_SET operations
     uint32_t n_heaps;            // MODE_SET
+    const unsigned long long *req_base;   // MODE_SET cursor DELs: output base
+    unsigned long long *req_cursor;       //   and running count, per request
 };
 
 // Block-shared scalars that carry decisions between the control warp and the
@@ -1006,7 +1008,7 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
 template <typename K, int IPT>
 __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t want, unsigned long long out_off, unsigned long long ref,
-                       uint32_t *count_out)
+                       uint32_t *count_out, long long req)
 {
     const uint32_t k = p.k;
     const bool ctrl = is_ctrl();
@@ -1030,6 +1032,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 unsigned long long rem = p.n > done ? p.n - done : 0ull;
                 want = rem < want ? (uint32_t)rem : want;
                 out_off = done;
+            } else if (req >= 0) {
+                // one request's DELs fill its output contiguously, in the order
+                // they hold this heap's root
+                out_off = p.req_base[req] + p.req_cursor[req];
             }
             const uint32_t avail = m >= 1 ? k : s;
             const uint32_t take = want < avail ? want : avail;
@@ -1039,6 +1045,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 p.ctl->delivered = out_off + take;
                 if (p.out_total) *p.out_total = out_off + take;
                 if (take == 0 || out_off + take >= p.n) p.ctl->drained = 1u;
+            } else if (req >= 0) {
+                p.req_cursor[req] += take;
             }
             if (count_out) *count_out = take;
             take_ticket(p, H, sh, GHEAP_OP_DEL, take, p.mode == MODE_DELETE ? out_off : ref);
@@ -1406,7 +1414,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared sh;
     __shared__ HeapView<K> set_view;   // MODE_SET: the heap of the current op
-    __shared__ uint32_t set_kind, set_n, set_skip;
+    __shared__ uint32_t set_kind, set_n, set_skip, set_cursor;
     __shared__ unsigned long long set_off;
     const uint32_t k = p.k;
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
@@ -1429,12 +1437,18 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
                 const uint32_t hid = d.heap < p.n_heaps ? d.heap : 0u;
                 set_view = p.table[hid];
                 set_kind = d.kind_n >> 24;
-                set_n = d.kind_n & 0xFFFFFFu;
+                set_cursor = (d.kind_n >> 23) & 1u;
+                set_n = d.kind_n & 0x7FFFFFu;
                 set_off = d.offset;
-                set_skip = d.heap >= p.n_heaps || set_n > k ||
-                           ld_relaxed(&set_view.hdr->err) != E_NONE;
-                // a malformed op is the named heap's sticky error
-                if (d.heap < p.n_heaps && set_n > k) set_err(set_view, E_STATE);
+                // ops on a missing heap, an empty slot or a heap with a sticky
+                // error are skipped; a malformed op is its heap's sticky error
+                set_skip = d.heap >= p.n_heaps || set_view.hdr == nullptr;
+                if (!set_skip) {
+                    const bool bad = set_n > k || (set_cursor && (set_kind != GHEAP_OP_DEL ||
+                                                                  p.req_cursor == nullptr));
+                    if (bad) set_err(set_view, E_STATE);
+                    set_skip = bad || ld_relaxed(&set_view.hdr->err) != E_NONE;
+                }
             } else if (!stop) {
                 stop = ld_relaxed(&H.hdr->err) != E_NONE;
                 if (!stop && p.mode == MODE_DELETE && ld_relaxed(&p.ctl->drained)) stop = 1;
@@ -1498,7 +1512,8 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
             }
         } else {
             ok = del_op<K, IPT>(p, H, sh, base, n, off, op,
-                                listed && p.out_counts ? p.out_counts + op : nullptr);
+                                listed && p.out_counts ? p.out_counts + op : nullptr,
+                                multi && set_cursor ? (long long)off : -1ll);
             if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
         }
         // one heap giving up ends a single-heap launch; in a set the other

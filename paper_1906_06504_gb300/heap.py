@@ -16,6 +16,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -5, -6
 FLAG_STATS = 1
 OP_INS, OP_DEL = 1, 2
+SET_CURSOR = 1 << 23
 
 # gheap_op, gheapset_op and gheap_log_entry of include/gheap.h
 OP_DTYPE = np.dtype([("kind", "<u4"), ("n", "<u4"), ("offset", "<u8")])
@@ -72,6 +73,9 @@ def lib():
             "heapset_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, vp]),
             "heapset_sync": (ctypes.c_int, [vp]),
             "heapset_reset": (ctypes.c_int, [vp, vp]),
+            "heapset_bind": (ctypes.c_int, [vp, u32, vp, vp]),
+            "heapset_unbind": (ctypes.c_int, [vp, u32, vp]),
+            "heapset_ops_req": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, vp, vp, vp]),
             "heapset_graph_create": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, ctypes.POINTER(vp)]),
             "heapset_graph_launch": (ctypes.c_int, [vp, vp]),
             "heapset_graph_destroy": (ctypes.c_int, [vp]),
@@ -260,7 +264,19 @@ class GHeapSet:
         self._s = h
         self.k = int(k)
         self.key_bytes = int(key_bytes)
-        self.heaps = [GHeap(c, _handle=L.heapset_heap(h, i)) for i, c in enumerate(capacities)]
+        self.heaps = [GHeap(c, _handle=L.heapset_heap(h, i)) if c else None
+                      for i, c in enumerate(capacities)]
+
+    def bind(self, i, heap, stream=None):
+        """Put a GHeap (same k and key width, kept by the caller) in empty slot i."""
+        _check(lib().heapset_bind(self._s, int(i), heap._h, _stream_ptr(stream)), "heapset_bind")
+        self.heaps[i] = GHeap(heap.capacity, _handle=heap._h.value)
+
+    def unbind(self, i, stream=None):
+        _check(lib().heapset_unbind(self._s, int(i), _stream_ptr(stream)), "heapset_unbind")
+        if self.heaps[i] is not None:
+            self.heaps[i]._h = None
+        self.heaps[i] = None
 
     def set_launch(self, ctas=0, items_per_thread=8):
         _check(lib().heapset_set_launch(self._s, int(ctas), int(items_per_thread)),
@@ -279,6 +295,14 @@ class GHeapSet:
     def ops(self, ops_dev, in_keys, out_keys, counts=None, stream=None):
         n_ops, o, i, ou, c = self._ptrs(ops_dev, in_keys, out_keys, counts)
         _check(lib().heapset_ops(self._s, o, n_ops, i, ou, c, _stream_ptr(stream)), "heapset_ops")
+
+    def ops_req(self, ops_dev, in_keys, out_keys, counts, req_base, req_cursor, stream=None):
+        """ops() with per-request cursors for SET_CURSOR DELs (uint64 tensors)."""
+        n_ops, o, i, ou, c = self._ptrs(ops_dev, in_keys, out_keys, counts)
+        _check(lib().heapset_ops_req(self._s, o, n_ops, i, ou, c,
+                                     ctypes.c_void_p(req_base.data_ptr()),
+                                     ctypes.c_void_p(req_cursor.data_ptr()),
+                                     _stream_ptr(stream)), "heapset_ops_req")
 
     def graph(self, ops_dev, in_keys, out_keys, counts=None):
         """A captured CUDA graph of ops(); launch() replays it."""
@@ -300,7 +324,8 @@ class GHeapSet:
     def close(self):
         if getattr(self, "_s", None):
             for h in self.heaps:
-                h._h = None
+                if h is not None:
+                    h._h = None
             lib().heapset_destroy(self._s)
             self._s = None
 
