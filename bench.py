@@ -150,6 +150,117 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
+def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, seed_off=0):
+    """SURVEY config 2, mixed part: prefill 2^24 keys, then 2^16 ins-del pairs
+    of k keys issued to all blocks at once (Section 5.5 ins-del pairs)."""
+    from paper_1906_06504_gb300 import inputs
+    from paper_1906_06504_gb300.heap import GHeap, OP_DTYPE, OP_INS, OP_DEL
+    pre = inputs.keys_u32(inputs.config_seed(2) + 100 + seed_off, n_prefill)
+    stream_keys = inputs.keys_u32(inputs.config_seed(2) + 200 + seed_off, n_pairs * k)
+    ops = np.zeros(2 * n_pairs, dtype=OP_DTYPE)
+    ops["kind"][0::2] = OP_INS
+    ops["kind"][1::2] = OP_DEL
+    ops["n"] = k
+    ops["offset"][0::2] = np.arange(n_pairs, dtype=np.uint64) * k
+    ops["offset"][1::2] = np.arange(n_pairs, dtype=np.uint64) * k
+    d_ops = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    d_pre = torch.from_numpy(pre.view(np.int32)).cuda()
+    d_in = torch.from_numpy(stream_keys.view(np.int32)).cuda()
+    d_out = torch.empty(n_pairs * k, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(2 * n_pairs, dtype=torch.int32, device="cuda")
+    with GHeap(capacity=n_prefill + n_pairs * k, k=k) as h:
+        h.set_launch(ctas=ctas, items_per_thread=ipt)
+        h.insert(d_pre)
+        h.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.ops(d_ops, d_in, d_out, counts)
+        e1.record()
+        torch.cuda.synchronize()
+        h.sync()
+        ms = e0.elapsed_time(e1)
+        assert h.size() == n_prefill
+    moved = int(counts.sum().item())
+    return {"workload": "prefill 2^24, then 2^16 ins-del pairs of k=1024 keys, all blocks",
+            "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}
+
+
+def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
+    """SURVEY config 5, batched part: 256 heaps with log-uniform sizes 2^10 to
+    2^22 keys; one launch inserts all of them, one launch deletes all, both
+    replayed from captured CUDA graphs; k and the merge width autotuned."""
+    from paper_1906_06504_gb300 import inputs, tune as tuner
+    from paper_1906_06504_gb300.heap import GHeapSet, OP_INS, OP_DEL
+    sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
+    total = int(sizes.sum())
+    keys = inputs.keys_u32(inputs.config_seed(5), total)
+    if tune:
+        best, table = tuner.autotune_set(sizes, keys, scale=0.125)
+    else:
+        best, table = {"k": 1024, "items_per_thread": 8}, []
+    k, ipt = best["k"], best["items_per_thread"]
+    ins = inputs.set_phase_ops(sizes, k, OP_INS)
+    dele = inputs.set_phase_ops(sizes, k, OP_DEL)
+    d_ins = torch.from_numpy(ins.view(np.uint8).copy()).cuda()
+    d_del = torch.from_numpy(dele.view(np.uint8).copy()).cuda()
+    d_keys = torch.from_numpy(keys.view(np.int32)).cuda()
+    d_out = torch.empty(total, dtype=torch.int32, device="cuda")
+    with GHeapSet([int(x) for x in sizes], k=k) as hs:
+        hs.set_launch(items_per_thread=ipt)
+        g_ins = hs.graph(d_ins, d_keys, None)
+        g_del = hs.graph(d_del, None, d_out)
+        g_ins.launch()
+        g_del.launch()
+        torch.cuda.synchronize()
+        hs.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g_ins.launch()
+            g_del.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        hs.sync()
+        ms = e0.elapsed_time(e1) / steps
+        # every heap ends empty; sampled heaps returned exactly their input
+        assert all(h.size() == 0 for h in hs.heaps)
+        out = d_out.cpu().numpy().view(np.uint32)
+        base = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        for hid in np.linspace(0, n_heaps - 1, verify_heaps).astype(int):
+            seg = slice(base[hid], base[hid] + sizes[hid])
+            assert np.array_equal(np.sort(out[seg]), np.sort(keys[seg]))
+        g_ins.close()
+        g_del.close()
+    return {"workload": "256 heaps, log-uniform 2^10..2^22 keys (%d total), insert-all + "
+                        "deleteMin-all, one launch each, CUDA-graph replay" % total,
+            "value": 2.0 * total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "k": k, "items_per_thread": ipt, "autotune": table}
+
+
+def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256):
+    """SURVEY config 5, served part: Poisson arrivals of insert / deleteMin
+    requests of 1..4096 keys over 256 heaps, continuously batched."""
+    from paper_1906_06504_gb300 import inputs
+    from paper_1906_06504_gb300.serve import HeapServer, latency_summary, poisson_requests
+    sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
+    caps = [int(max(s, 1 << 18)) for s in sizes]
+    reqs = poisson_requests(inputs.config_seed(5) + 7, n_requests, n_heaps, rate, max_keys=4096)
+    srv = HeapServer(caps, k=1024, max_batch_keys=1 << 22)
+    try:
+        srv.preadmit(range(n_heaps))
+        srv.run(reqs, realtime=True)
+        stats = dict(srv.stats)
+    finally:
+        srv.close()
+    summ = latency_summary(reqs)
+    summ.update({"arrival_rate_per_s": rate, "heaps": n_heaps, "batches": stats["batches"],
+                 "workload": "Poisson arrivals, 1..4096 keys, 50/50 insert/deleteMin, "
+                             "256 heaps, k=1024"})
+    return summ
+
+
 def run_gpu(args):
     import torch
     from paper_1906_06504_gb300 import build, inputs
@@ -264,6 +375,11 @@ def run_gpu(args):
                          "uniform stream, sequential binary heap, %.1f s" % dt}
 
     heap.close()
+    extras = {}
+    if not args.skip_extras:
+        extras["mixed"] = run_mixed(torch, ipt=args.ipt)
+        extras["batched"] = run_batched(torch, tune=not args.no_tune)
+        extras["serve"] = run_serve(torch)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -285,6 +401,9 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "stats_delete": st_del, "stats_insert": st_ins,
         }
+        line.update(extras)
+        if "batched" in extras:
+            line["batched"]["vs_plain"] = extras["batched"]["value"] / value
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -302,6 +421,9 @@ def main():
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--ipt", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the headline single-heap workload")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

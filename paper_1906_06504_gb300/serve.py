@@ -118,6 +118,13 @@ class HeapServer:
         self.stats["admitted"] += 1
         return True
 
+    def preadmit(self, heaps):
+        """Admits heaps ahead of their first request (allocation is not free)."""
+        for h in heaps:
+            if not self._admit(int(h), set()):
+                raise RuntimeError("heap %d does not fit the HBM budget" % h)
+        self.torch.cuda.synchronize()
+
     # -- one batch
     def _select(self, pending):
         """At most one request per heap, in arrival order; a heap's later
