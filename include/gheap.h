@@ -44,6 +44,7 @@ typedef struct gheap_s *gheap_t;
 #define GHEAP_ERR_TIMEOUT (-4) /* a bounded lock wait gave up (sticky)     */
 #define GHEAP_ERR_CUDA (-5)    /* a CUDA runtime call failed               */
 #define GHEAP_ERR_STATE (-6)   /* device found an impossible node state    */
+#define GHEAP_ERR_TOO_LARGE (-7) /* beyond the fixed scratch of heap_sort_noalloc */
 
 /* heap_create flags */
 #define GHEAP_FLAG_STATS 1u    /* count node loads/stores and merges       */
@@ -258,6 +259,38 @@ int heapset_graph_create(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops,
                          gheapset_graph_t *out);
 int heapset_graph_launch(gheapset_graph_t g, void *stream);
 int heapset_graph_destroy(gheapset_graph_t g);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is an
+ * interface for callers that must not allocate device memory -- code whose
+ * device memory is all reserved up front by a pool or budget it does not own,
+ * and paths that cannot accept the latency or the implicit synchronization of
+ * a cudaMalloc.
+ *
+ * heap_sort_noalloc inserts the n uint32_t keys of d_in (device) into a
+ * temporary generalized heap with k = 1024 and deletes them all into d_out
+ * (device, n keys, ascending) -- the same kernels and the same result as
+ * heap_create + heap_insert + heap_delete_min.  Instead of allocating, the
+ * heap lives in one fixed scratch array compiled into this library (about
+ * 4.2 MB of device memory, held by every GPU that loads the library until the
+ * process exits).  The caller passes only the input and output buffers.
+ *
+ *   - n may be at most GHEAP_NOALLOC_MAX_KEYS; larger n returns
+ *     GHEAP_ERR_TOO_LARGE and enqueues nothing.  n = 0 does nothing.
+ *   - The first call on each device looks up that device's address of the
+ *     scratch array (a synchronous CUDA runtime query) with that device
+ *     current; make that first call before any stream capture.  Later calls
+ *     only enqueue work on `stream` and allocate nothing.
+ *   - Every call shares the one scratch array: calls whose work overlaps on
+ *     the GPU (different streams, or other host threads) race and corrupt
+ *     each other.  Each call clears the heap state it needs, so a call never
+ *     depends on what the previous call left in the array.
+ *   - Device-side lock waits are bounded as for heap_insert; such a failure
+ *     is not reported by this entry point (the output would then be
+ *     incomplete).
+ * ------------------------------------------------------------------------ */
+#define GHEAP_NOALLOC_MAX_KEYS (1ull << 20)
+int heap_sort_noalloc(const uint32_t *d_in, uint32_t *d_out, uint64_t n, void *stream);
 
 /* Human-readable text of an error code. */
 const char *heap_strerror(int code);

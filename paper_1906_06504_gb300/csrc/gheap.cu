@@ -193,6 +193,7 @@ const char *heap_strerror(int code)
     case GHEAP_ERR_TIMEOUT: return "a bounded lock wait gave up";
     case GHEAP_ERR_CUDA: return "CUDA runtime error";
     case GHEAP_ERR_STATE: return "impossible node state observed on the device";
+    case GHEAP_ERR_TOO_LARGE: return "more keys than the fixed scratch of heap_sort_noalloc holds";
     default: return "unknown error";
     }
 }
@@ -763,6 +764,91 @@ int heapset_graph_destroy(gheapset_graph_t G)
     if (G->graph) cudaGraphDestroy(G->graph);
     free(G);
     return GHEAP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// allocation-free sort (heap_sort_noalloc): the heap in a fixed scratch array
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+constexpr uint32_t NA_K = 1024;
+constexpr uint32_t NA_MAX_NODES = (uint32_t)(GHEAP_NOALLOC_MAX_KEYS / NA_K) + 1;
+constexpr size_t NA_SLOTS = (size_t)NA_MAX_NODES + 1;
+constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_OFF_HDR = 0;
+constexpr size_t NA_OFF_CTL = na_round(sizeof(gh::Hdr));
+constexpr size_t NA_OFF_CNT = NA_OFF_CTL + na_round(sizeof(gh::Ctl));
+constexpr size_t NA_OFF_STATE = NA_OFF_CNT + 256;
+constexpr size_t NA_OFF_BUF = NA_OFF_STATE + na_round(NA_SLOTS * sizeof(uint32_t));
+constexpr size_t NA_OFF_KEYS = NA_OFF_BUF + na_round(NA_K * sizeof(uint32_t));
+constexpr size_t NA_BYTES = NA_OFF_KEYS + NA_SLOTS * NA_K * sizeof(uint32_t);
+
+constexpr int NA_MAX_DEVICES = 64;
+unsigned char *na_base[NA_MAX_DEVICES];   // per-device address of the array
+
+}  // namespace
+
+// Header, launch counters, a count word, node states, the partial buffer and
+// (max_nodes + 1) node batches of one k = 1024 heap, each section 256-aligned.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+extern "C" {
+
+int heap_sort_noalloc(const uint32_t *d_in, uint32_t *d_out, uint64_t n, void *stream)
+{
+    if (n > GHEAP_NOALLOC_MAX_KEYS) return GHEAP_ERR_TOO_LARGE;
+    if (n == 0) return GHEAP_OK;
+    if (!d_in || !d_out) return GHEAP_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return GHEAP_ERR_ARG;
+    unsigned char *base = na_base[dev];
+    if (!base) {
+        // once per device, with that device current: the host-side name of
+        // the array is not its device address
+        if (cudaGetSymbolAddress((void **)&base, g_noalloc_scratch) != cudaSuccess || !base)
+            return GHEAP_ERR_CUDA;
+        na_base[dev] = base;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the root word, ticket counter, error word, launch counters and node
+    // states must start at zero; keys and the partial buffer need not
+    if (cudaMemsetAsync(base, 0, NA_OFF_BUF, s) != cudaSuccess) return GHEAP_ERR_CUDA;
+    gh::Params<uint32_t> p;
+    memset(&p, 0, sizeof(p));
+    p.h.keys = reinterpret_cast<uint32_t *>(base + NA_OFF_KEYS);
+    p.h.state = reinterpret_cast<uint32_t *>(base + NA_OFF_STATE);
+    p.h.buf = reinterpret_cast<uint32_t *>(base + NA_OFF_BUF);
+    p.h.hdr = reinterpret_cast<gh::Hdr *>(base + NA_OFF_HDR);
+    p.h.max_nodes = NA_MAX_NODES;
+    p.ctl = reinterpret_cast<gh::Ctl *>(base + NA_OFF_CTL);
+    p.k = NA_K;
+    p.timeout_ns = 2000000000ull;
+    Shape sp;
+    sp.k = NA_K;
+    sp.ipt = 8;
+    sp.ctas = 0;
+    sp.sm_count = sms;
+    sp.d_ctl = p.ctl;
+    const uint64_t n_ops = (n + NA_K - 1) / NA_K;
+    p.mode = gh::MODE_INSERT;
+    p.call_id = 1;
+    p.in = d_in;
+    p.n = n;
+    int rc = launch_k<uint32_t>(sp, p, n_ops, s);
+    if (rc != GHEAP_OK) return rc;
+    p.mode = gh::MODE_DELETE;
+    p.call_id = 2;
+    p.in = nullptr;
+    p.out = d_out;
+    p.out_total = reinterpret_cast<unsigned long long *>(base + NA_OFF_CNT);
+    return launch_k<uint32_t>(sp, p, n_ops, s);
 }
 
 int heap_debug_hold_root(gheap_t h, void *stream)

@@ -13,7 +13,8 @@ import numpy as np
 from . import build as _build
 
 OK = 0
-ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -5, -6
+ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE, ERR_TOO_LARGE = (
+    -1, -2, -3, -4, -5, -6, -7)
 FLAG_STATS = 1
 OP_INS, OP_DEL = 1, 2
 SET_CURSOR = 1 << 23
@@ -65,6 +66,7 @@ def lib():
             "heap_slot_to_node": (u64, [u64]),
             "heap_get_stats": (ctypes.c_int, [vp, u64p, u32]),
             "heap_debug_hold_root": (ctypes.c_int, [vp, vp]),
+            "heap_sort_noalloc": (ctypes.c_int, [vp, vp, u64, vp]),
             "heapset_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64p, u32, u32, u32, u64]),
             "heapset_destroy": (ctypes.c_int, [vp]),
             "heapset_heap": (vp, [vp, u32]),
