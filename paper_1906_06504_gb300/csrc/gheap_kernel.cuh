@@ -997,6 +997,7 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
     if (lk[0] == ST_AVAIL) g2s(dl, H.keys + (size_t)sl * k, k, lane, 32u);
     if (lk[1] == ST_AVAIL) g2s(dr, H.keys + (size_t)sr * k, k, lane, 32u);
     cp_async_commit();
+    if (lane == 0) stat_add(sh, STAT_LOADS, (lk[0] == ST_AVAIL) + (lk[1] == ST_AVAIL));
     cp_async_wait();
 }
 
