@@ -105,6 +105,15 @@ int heap_set_timeout(gheap_t h, uint64_t ns);
  * heap could exceed capacity_keys. */
 int heap_insert(gheap_t h, const void *d_keys, uint64_t n, void *stream);
 
+/* heap_insert with the key count in device memory: inserts the first
+ * min(*d_n, max_n) keys of d_keys (device), *d_n being read when the work
+ * runs on `stream`, so a kernel enqueued before it may produce the count.
+ * Nothing synchronizes.  The capacity is checked on the device only: an
+ * insert that finds no free node sets the sticky GHEAP_ERR_FULL (reported by
+ * heap_sync and later calls), and the keys of that insert are lost. */
+int heap_insert_dev(gheap_t h, const void *d_keys, const uint64_t *d_n, uint64_t max_n,
+                    void *stream);
+
 /* Deletes the min(n, size) smallest keys (Section 3.2.1 DEL) as ceil(n/k)
  * DEL operations and writes them to d_out in the order the operations held
  * the root, which is ascending when no insert runs concurrently.  When

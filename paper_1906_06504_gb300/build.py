@@ -1,7 +1,8 @@
 """Builds the CUDA shared library behind include/gheap.h, in-tree.
 
 nvcc -gencode arch=compute_103a,code=sm_103a (GB300) -> libgheap.so next to
-this file.  Rebuilds when a source is newer than the library.
+this file: gheap.cu (the heap and its C ABI) and apps.cu (applications built
+on that ABI).  Rebuilds when a source is newer than the library.
 """
 import glob
 import os
@@ -15,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libgheap.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared"]
+COMPILE = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -44,15 +45,37 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
-    """Compiles libgheap.so (all .cu files in csrc/ in one nvcc call)."""
+    """Compiles libgheap.so: every .cu file in csrc/ to an object, in parallel,
+    then one link."""
     if not force and up_to_date():
         return LIB
-    tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc()] + ARCH + FLAGS + ["-I" + INCLUDE, "-I" + CSRC, "-o", tmp] + sources()
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = "%d" % os.getpid()
+    objs, procs = [], []
+    for src in sources():
+        obj = os.path.join(PKG, "." + os.path.basename(src) + "." + tag + ".o")
+        cmd = [nvcc()] + ARCH + COMPILE + ["-I" + INCLUDE, "-I" + CSRC, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd))
+        objs.append(obj)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    try:
+        for cmd, p in procs:
+            if p.wait() != 0:
+                raise subprocess.CalledProcessError(p.returncode, cmd)
+        tmp = LIB + "." + tag + ".tmp"
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    finally:
+        for cmd, p in procs:
+            if p.poll() is None:
+                p.kill()
+                p.wait()
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return LIB
 
 

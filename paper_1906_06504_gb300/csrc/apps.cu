@@ -1,0 +1,425 @@
+// apps.cu -- applications of the concurrent heap (arXiv 1906.06504, Section
+// 5.7), written against the public C ABI of gheap.h like any other caller.
+//
+// SSSP (Section 5.7.1): the heap holds the active vertices keyed by
+// (distance << 32 | vertex).  One iteration is four stream-ordered steps,
+// none of which returns to the host:
+//   heap_delete_min(batch)  ->  sssp_relax  ->  sssp_relax_heavy  ->  heap_insert_dev
+// sssp_relax drops stale keys and relaxes the out-edges of the others with a
+// block-level load balance (a scan of the degrees, then one edge per thread);
+// vertices of more than HEAVY out-edges are queued for sssp_relax_heavy,
+// which spreads each one over the whole grid.  The last block of
+// sssp_relax_heavy keeps the device's count of live heap keys and writes it
+// to a ring in mapped host memory, so the host learns that the heap ran empty
+// a few iterations later without draining the stream every iteration.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gheap_apps.h"
+
+namespace {
+
+constexpr int RT = 256;                       // threads of a relax block
+constexpr unsigned long long HEAVY = 2048;    // out-degree spread over the grid
+constexpr int RING = 8;                       // ring slots (iterations tracked)
+constexpr int LAG = 4;                        // iterations in flight before the host waits
+constexpr unsigned FULL = 0xffffffffu;
+
+// Device counters of one run.
+struct Ctr {
+    unsigned long long popped;      // keys the iteration's deleteMin returned
+    unsigned long long front[2];    // insert-buffer fill, by iteration parity
+    unsigned long long n_heavy;     // vertices queued for sssp_relax_heavy
+    unsigned long long live;        // keys in the heap after the iteration
+    unsigned long long stalled;     // 1: empty deleteMin from a non-empty heap,
+                                    // 2: insert buffer overflow, 3: count underflow
+    unsigned long long done;        // blocks of sssp_relax_heavy finished
+    unsigned long long visited, edges, inserted, deleted;
+};
+
+struct Graph {
+    const unsigned long long *rowptr;
+    const uint32_t *col;
+    const uint32_t *w;
+    uint32_t *dist;
+};
+
+// Lowers dist[u] to nd if nd is smaller; true when this call lowered it.
+// dist only decreases, so a plain load that misses a newer value sees a
+// larger one and never skips a lowering that the atomic would have made.
+__device__ __forceinline__ bool relax(uint32_t *dist, uint32_t u, unsigned long long nd)
+{
+    if (nd >= 0xFFFFFFFFull) return false;    // not representable: unreachable
+    const uint32_t n32 = (uint32_t)nd;
+    if (n32 >= __ldcg(dist + u)) return false;
+    return n32 < atomicMin(dist + u, n32);
+}
+
+// Appends `key` for the lanes with `push` set; the whole warp calls it.
+__device__ __forceinline__ void append(bool push, unsigned long long key, unsigned long long *front,
+                                       unsigned long long *n_front, unsigned long long cap)
+{
+    const unsigned mask = __ballot_sync(FULL, push);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(n_front, (unsigned long long)__popc(mask));
+    base = __shfl_sync(FULL, base, leader);
+    if (push) {
+        const unsigned long long pos = base + __popc(mask & ((1u << lane) - 1u));
+        if (pos < cap) front[pos] = key;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+__device__ __forceinline__ void add_stats(Ctr *c, unsigned long long visited,
+                                          unsigned long long edges, unsigned long long ins)
+{
+    visited = warp_sum(visited);
+    edges = warp_sum(edges);
+    ins = warp_sum(ins);
+    if ((threadIdx.x & 31) == 0) {
+        if (visited) atomicAdd(&c->visited, visited);
+        if (edges) atomicAdd(&c->edges, edges);
+        if (ins) atomicAdd(&c->inserted, ins);
+    }
+}
+
+// Exclusive prefix sum of x over the block; *total gets the sum.
+__device__ __forceinline__ unsigned long long block_scan(unsigned long long x, unsigned long long *s_warp,
+                                                         unsigned long long *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long t = lane < RT / 32 ? s_warp[lane] : 0ull;
+        for (int o = 1; o < RT / 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < RT / 32) s_warp[lane] = t;
+    }
+    __syncthreads();
+    *total = s_warp[RT / 32 - 1];
+    return (wid ? s_warp[wid - 1] : 0ull) + inc - x;
+}
+
+__global__ void sssp_init(uint32_t *dist, uint32_t source, unsigned long long *front, Ctr *c)
+{
+    dist[source] = 0;
+    front[0] = (unsigned long long)source;    // distance 0
+    c->live = 1;
+}
+
+// Steps 2-3 of an iteration for the popped keys of degree <= HEAVY.
+__global__ void __launch_bounds__(RT) sssp_relax(Graph g, const unsigned long long *popped, Ctr *c,
+                                                 uint32_t par, unsigned long long *front,
+                                                 unsigned long long cap, unsigned long long *heavy)
+{
+    __shared__ unsigned long long s_off[RT + 1];
+    __shared__ unsigned long long s_beg[RT];
+    __shared__ uint32_t s_d[RT];
+    __shared__ unsigned long long s_warp[RT / 32];
+    const unsigned long long np = c->popped;
+    unsigned long long *n_front = &c->front[par];
+    unsigned long long visited = 0, edges = 0, ins = 0;
+    for (unsigned long long chunk = (unsigned long long)blockIdx.x * RT; chunk < np;
+         chunk += (unsigned long long)gridDim.x * RT) {
+        const unsigned long long i = chunk + threadIdx.x;
+        unsigned long long deg = 0, beg = 0;
+        uint32_t d = 0;
+        if (i < np) {
+            const unsigned long long key = popped[i];
+            const uint32_t v = (uint32_t)key;
+            d = (uint32_t)(key >> 32);
+            if (d == __ldcg(g.dist + v)) {            // else stale: a lower key of v exists
+                visited++;
+                beg = g.rowptr[v];
+                deg = g.rowptr[v + 1] - beg;
+                if (deg > HEAVY) {
+                    heavy[atomicAdd(&c->n_heavy, 1ull)] = key;
+                    deg = 0;
+                }
+            }
+        }
+        unsigned long long total;
+        const unsigned long long off = block_scan(deg, s_warp, &total);
+        s_off[threadIdx.x] = off;
+        s_beg[threadIdx.x] = beg;
+        s_d[threadIdx.x] = d;
+        if (threadIdx.x == 0) s_off[RT] = total;
+        __syncthreads();
+        for (unsigned long long e0 = 0; e0 < total; e0 += RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            bool push = false;
+            unsigned long long key = 0;
+            if (e < total) {
+                int lo = 0, hi = RT;                  // s_off[lo] <= e < s_off[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= e) lo = mid;
+                    else hi = mid;
+                }
+                const unsigned long long edge = s_beg[lo] + (e - s_off[lo]);
+                const uint32_t u = g.col[edge];
+                const unsigned long long nd = (unsigned long long)s_d[lo] + g.w[edge];
+                edges++;
+                if (relax(g.dist, u, nd)) {
+                    push = true;
+                    key = (nd << 32) | u;
+                    ins++;
+                }
+            }
+            append(push, key, front, n_front, cap);
+        }
+        __syncthreads();
+    }
+    add_stats(c, visited, edges, ins);
+}
+
+// Step 3 for the queued high-degree vertices, then the iteration's
+// bookkeeping in the last block to finish.
+__global__ void __launch_bounds__(RT) sssp_relax_heavy(Graph g, Ctr *c, uint32_t par,
+                                                       unsigned long long *front,
+                                                       unsigned long long cap,
+                                                       const unsigned long long *heavy,
+                                                       unsigned long long *ring, uint32_t slot)
+{
+    __shared__ bool last;
+    const unsigned long long nh = c->n_heavy;
+    unsigned long long *n_front = &c->front[par];
+    unsigned long long edges = 0, ins = 0;
+    for (unsigned long long h = 0; h < nh; h++) {
+        const unsigned long long hk = heavy[h];
+        const uint32_t v = (uint32_t)hk;
+        const unsigned long long d = hk >> 32;
+        const unsigned long long beg = g.rowptr[v], deg = g.rowptr[v + 1] - beg;
+        for (unsigned long long e0 = (unsigned long long)blockIdx.x * RT; e0 < deg;
+             e0 += (unsigned long long)gridDim.x * RT) {
+            const unsigned long long e = e0 + threadIdx.x;
+            bool push = false;
+            unsigned long long key = 0;
+            if (e < deg) {
+                const uint32_t u = g.col[beg + e];
+                const unsigned long long nd = d + g.w[beg + e];
+                edges++;
+                if (relax(g.dist, u, nd)) {
+                    push = true;
+                    key = (nd << 32) | u;
+                    ins++;
+                }
+            }
+            append(push, key, front, n_front, cap);
+        }
+    }
+    add_stats(c, 0, edges, ins);
+
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&c->done, 1ull) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    volatile Ctr *vc = c;
+    const unsigned long long np = vc->popped, live0 = vc->live;
+    unsigned long long nf = vc->front[par], stalled = vc->stalled;
+    if (nf > cap && !stalled) stalled = 2;
+    if (nf > cap) nf = cap;
+    if (np > live0 && !stalled) stalled = 3;
+    if (np == 0 && live0 > 0 && !stalled) stalled = 1;
+    const unsigned long long live = np > live0 ? nf : live0 - np + nf;
+    vc->live = live;
+    vc->stalled = stalled;
+    vc->deleted = vc->deleted + np;
+    vc->front[par ^ 1u] = 0;          // the next iteration's insert buffer
+    vc->n_heavy = 0;
+    vc->done = 0;
+    volatile unsigned long long *r = ring;
+    r[2 * slot] = live;
+    r[2 * slot + 1] = stalled;
+    __threadfence_system();
+}
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? GHEAP_OK : GHEAP_ERR_CUDA; }
+
+}  // namespace
+
+struct sssp_s {
+    int device;
+    int sm_count;
+    uint32_t n_vertices;
+    uint64_t n_edges;
+    uint32_t batch;
+    gheap_t heap;
+    unsigned long long *d_batch;    // keys of one deleteMin
+    unsigned long long *d_front;    // keys of one insert
+    unsigned long long *d_heavy;    // high-degree keys of one iteration
+    unsigned long long front_cap;
+    Ctr *d_ctr;
+    unsigned long long *h_ring;     // mapped host memory, 2 words per slot
+    unsigned long long *d_ring;
+    cudaEvent_t ev[RING];
+};
+
+extern "C" {
+
+int sssp_destroy(sssp_t s)
+{
+    if (!s) return GHEAP_ERR_ARG;
+    cudaSetDevice(s->device);
+    if (s->heap) heap_destroy(s->heap);
+    cudaFree(s->d_batch);
+    cudaFree(s->d_front);
+    cudaFree(s->d_heavy);
+    cudaFree(s->d_ctr);
+    if (s->h_ring) cudaFreeHost(s->h_ring);
+    for (int i = 0; i < RING; i++)
+        if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    free(s);
+    return GHEAP_OK;
+}
+
+int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, uint32_t batch,
+                uint64_t heap_capacity)
+{
+    if (!out) return GHEAP_ERR_ARG;
+    *out = nullptr;
+    if (n_vertices == 0 || n_vertices == 0xFFFFFFFFu || batch == 0) return GHEAP_ERR_ARG;
+    sssp_t s = (sssp_t)calloc(1, sizeof(sssp_s));
+    if (!s) return GHEAP_ERR_OOM;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { free(s); return GHEAP_ERR_CUDA; }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) { free(s); return GHEAP_ERR_CUDA; }
+    s->sm_count = prop.multiProcessorCount;
+    s->n_vertices = n_vertices;
+    s->n_edges = n_edges;
+    s->batch = batch;
+    s->front_cap = n_edges ? n_edges : 1;
+    if (heap_capacity == 0) heap_capacity = n_edges + n_vertices + 1;
+    int rc = heap_create(&s->heap, heap_capacity, k, 8, 0, 0);
+    if (rc != GHEAP_OK) { s->heap = nullptr; sssp_destroy(s); return rc; }
+    bool ok = cudaMalloc(&s->d_batch, (size_t)batch * 8) == cudaSuccess &&
+              cudaMalloc(&s->d_front, (size_t)s->front_cap * 8) == cudaSuccess &&
+              cudaMalloc(&s->d_heavy, (size_t)batch * 8) == cudaSuccess &&
+              cudaMalloc(&s->d_ctr, sizeof(Ctr)) == cudaSuccess;
+    if (!ok) { sssp_destroy(s); return GHEAP_ERR_OOM; }
+    if (cudaHostAlloc(&s->h_ring, 2 * RING * sizeof(unsigned long long), cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(&s->d_ring, s->h_ring, 0) != cudaSuccess) {
+        sssp_destroy(s);
+        return GHEAP_ERR_CUDA;
+    }
+    for (int i = 0; i < RING; i++) {
+        if (cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            sssp_destroy(s);
+            return GHEAP_ERR_CUDA;
+        }
+    }
+    *out = s;
+    return GHEAP_OK;
+}
+
+int sssp_set_launch(sssp_t s, uint32_t ctas, uint32_t items_per_thread)
+{
+    if (!s) return GHEAP_ERR_ARG;
+    return heap_set_launch(s->heap, ctas, items_per_thread);
+}
+
+int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const uint32_t *d_w,
+             uint32_t n_vertices, uint64_t n_edges, uint32_t source, uint32_t *d_dist,
+             sssp_stats *stats, void *stream)
+{
+    if (!s || !d_rowptr || !d_dist) return GHEAP_ERR_ARG;
+    if (n_vertices == 0 || n_vertices > s->n_vertices || n_edges > s->n_edges) return GHEAP_ERR_ARG;
+    if (source >= n_vertices) return GHEAP_ERR_ARG;
+    if (n_edges && (!d_col || !d_w)) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(s->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctr *c = s->d_ctr;
+    Graph g;
+    g.rowptr = reinterpret_cast<const unsigned long long *>(d_rowptr);
+    g.col = d_col;
+    g.w = d_w;
+    g.dist = d_dist;
+
+    int rc = heap_reset(s->heap, stream);
+    if (rc != GHEAP_OK) return rc;
+    cudaError_t e = cudaMemsetAsync(d_dist, 0xFF, (size_t)n_vertices * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, sizeof(Ctr), st);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    sssp_init<<<1, 1, 0, st>>>(d_dist, source, s->d_front, c);
+    if ((e = cudaGetLastError()) != cudaSuccess) return GHEAP_ERR_CUDA;
+    rc = heap_insert(s->heap, s->d_front, 1, stream);
+    if (rc != GHEAP_OK) return rc;
+
+    // relax grids: one chunk of RT popped keys per block, and a grid-wide
+    // spread for the high-degree vertices
+    const unsigned relax_grid =
+        (unsigned)((s->batch + RT - 1) / RT < (uint64_t)s->sm_count * 8 ? (s->batch + RT - 1) / RT
+                                                                         : (uint64_t)s->sm_count * 8);
+    const unsigned heavy_grid = (unsigned)s->sm_count * 4;
+    const unsigned long long cap = n_edges ? n_edges : 1;
+
+    uint64_t issued = 0, ended_at = 0;
+    unsigned long long stalled = 0;
+    bool done = false;
+    while (!done) {
+        const uint32_t par = (uint32_t)(issued & 1u), slot = (uint32_t)(issued % RING);
+        rc = heap_delete_min(s->heap, s->d_batch, s->batch, reinterpret_cast<uint64_t *>(&c->popped),
+                             stream);
+        if (rc != GHEAP_OK) return rc;
+        sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy);
+        sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy,
+                                                   s->d_ring, slot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return GHEAP_ERR_CUDA;
+        if (cudaEventRecord(s->ev[slot], st) != cudaSuccess) return GHEAP_ERR_CUDA;
+        rc = heap_insert_dev(s->heap, s->d_front, reinterpret_cast<const uint64_t *>(&c->front[par]),
+                             cap, stream);
+        if (rc != GHEAP_OK) return rc;
+        issued++;
+        // wait for the iteration issued LAG ago and read its live-key count
+        while (issued - ended_at >= (uint64_t)LAG) {
+            const uint32_t js = (uint32_t)(ended_at % RING);
+            if (cudaEventSynchronize(s->ev[js]) != cudaSuccess) return GHEAP_ERR_CUDA;
+            const volatile unsigned long long *r = s->h_ring;
+            const unsigned long long live = r[2 * js];
+            stalled = r[2 * js + 1];
+            ended_at++;
+            if (live == 0 || stalled) {
+                done = true;
+                break;
+            }
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GHEAP_ERR_CUDA;
+    rc = heap_sync(s->heap);
+    if (rc != GHEAP_OK) return rc;
+    if (stalled) return GHEAP_ERR_STATE;
+    if (stats) {
+        Ctr hc;
+        if (cudaMemcpy(&hc, c, sizeof(Ctr), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GHEAP_ERR_CUDA;
+        stats->iterations = ended_at;
+        stats->keys_deleted = hc.deleted;
+        stats->visited = hc.visited;
+        stats->edges = hc.edges;
+        stats->keys_inserted = hc.inserted;
+    }
+    return cuda_err(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -329,6 +329,33 @@ int heap_insert(gheap_t h, const void *d_keys, uint64_t n, void *stream)
                   (cudaStream_t)stream);
 }
 
+int heap_insert_dev(gheap_t h, const void *d_keys, const uint64_t *d_n, uint64_t max_n,
+                    void *stream)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (max_n == 0) return GHEAP_OK;
+    if (!d_keys || !d_n) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    // the count is not known here: the device checks the node storage (E_FULL),
+    // and the host bound saturates so that a later heap_insert re-reads the size
+    h->size_upper = max_n > h->capacity - h->size_upper ? h->capacity : h->size_upper + max_n;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t launch_ops = (max_n + h->k - 1) / h->k;
+    if (h->key_bytes == 4) {
+        gh::Params<uint32_t> p = base_params<uint32_t>(h, gh::MODE_INSERT);
+        p.in = static_cast<const uint32_t *>(d_keys);
+        p.n = max_n;
+        p.n_dev = reinterpret_cast<const unsigned long long *>(d_n);
+        return launch_k<uint32_t>(shape_of(h), p, launch_ops, s);
+    }
+    gh::Params<uint64_t> p = base_params<uint64_t>(h, gh::MODE_INSERT);
+    p.in = static_cast<const uint64_t *>(d_keys);
+    p.n = max_n;
+    p.n_dev = reinterpret_cast<const unsigned long long *>(d_n);
+    return launch_k<uint64_t>(shape_of(h), p, launch_ops, s);
+}
+
 int heap_delete_min(gheap_t h, void *d_out, uint64_t n, uint64_t *d_count, void *stream)
 {
     if (!h) return GHEAP_ERR_ARG;

@@ -147,6 +147,7 @@ struct Params {
     uint32_t n_heaps;            // MODE_SET
     const unsigned long long *req_base;   // MODE_SET cursor DELs: output base
     unsigned long long *req_cursor;       //   and running count, per request
+    const unsigned long long *n_dev;      // MODE_INSERT: key count in device memory
 };
 
 // Block-shared scalars that carry decisions between the control warp and the
@@ -1423,6 +1424,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     const HeapView<K> &H = multi ? set_view : p.h;
     if (threadIdx.x < N_STATS) sh.cnt[threadIdx.x] = 0;
 
+    if (p.n_dev) {
+        // the key count was produced on the device (at most p.n)
+        const unsigned long long nd = *p.n_dev;
+        p.n = nd < p.n ? nd : p.n;
+    }
     unsigned long long n_ops;
     if (p.mode == MODE_OPS || multi) n_ops = p.n_ops;
     else n_ops = (p.n + k - 1) / k;

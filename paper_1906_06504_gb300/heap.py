@@ -81,7 +81,13 @@ def lib():
             "heapset_graph_create": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, ctypes.POINTER(vp)]),
             "heapset_graph_launch": (ctypes.c_int, [vp, vp]),
             "heapset_graph_destroy": (ctypes.c_int, [vp]),
+            "heap_insert_dev": (ctypes.c_int, [vp, vp, vp, u64, vp]),
             "heap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            # gheap_apps.h
+            "sssp_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64, u32, u32, u64]),
+            "sssp_destroy": (ctypes.c_int, [vp]),
+            "sssp_set_launch": (ctypes.c_int, [vp, u32, u32]),
+            "sssp_run": (ctypes.c_int, [vp, vp, vp, vp, u32, u64, u32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -151,6 +157,16 @@ class GHeap:
         self._key_tensor(keys, "keys")
         _check(lib().heap_insert(self._h, ctypes.c_void_p(keys.data_ptr()), keys.numel(),
                                  _stream_ptr(stream)), "heap_insert")
+
+    def insert_dev(self, keys, count, stream=None):
+        """Inserts the first min(count[0], keys.numel()) keys; `count` is a
+        1-element int64 CUDA tensor read when the work runs."""
+        self._key_tensor(keys, "keys")
+        if not count.is_cuda or count.element_size() != 8:
+            raise ValueError("count must be a 1-element int64 CUDA tensor")
+        _check(lib().heap_insert_dev(self._h, ctypes.c_void_p(keys.data_ptr()),
+                                     ctypes.c_void_p(count.data_ptr()), keys.numel(),
+                                     _stream_ptr(stream)), "heap_insert_dev")
 
     def delete_min(self, n, out=None, count=None, stream=None):
         """Deletes up to n smallest keys into `out` (allocated if None).
