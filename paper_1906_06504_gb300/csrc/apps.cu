@@ -10,8 +10,10 @@
 // vertices of more than HEAVY out-edges are queued for sssp_relax_heavy,
 // which spreads each one over the whole grid.  The last block of
 // sssp_relax_heavy keeps the device's count of live heap keys and writes it
-// to a ring in mapped host memory, so the host learns that the heap ran empty
-// a few iterations later without draining the stream every iteration.
+// to mapped host memory.  The iterations are captured UNROLL at a time in two
+// CUDA graphs that the host launches alternately, reading the count left by
+// one graph while the other runs, so the stream never drains before the heap
+// is empty and the host issues one launch per UNROLL iterations.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -23,8 +25,7 @@ namespace {
 
 constexpr int RT = 256;                       // threads of a relax block
 constexpr unsigned long long HEAVY = 2048;    // out-degree spread over the grid
-constexpr int RING = 8;                       // ring slots (iterations tracked)
-constexpr int LAG = 4;                        // iterations in flight before the host waits
+constexpr int UNROLL = 4;                     // iterations per graph (even: parities alternate)
 constexpr unsigned FULL = 0xffffffffu;
 
 // Device counters of one run.
@@ -36,6 +37,7 @@ struct Ctr {
     unsigned long long stalled;     // 1: empty deleteMin from a non-empty heap,
                                     // 2: insert buffer overflow, 3: count underflow
     unsigned long long done;        // blocks of sssp_relax_heavy finished
+    unsigned long long iters;       // iterations whose deleteMin returned keys
     unsigned long long visited, edges, inserted, deleted;
 };
 
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(RT) sssp_relax_heavy(Graph g, Ctr *c, uint32_t
     vc->live = live;
     vc->stalled = stalled;
     vc->deleted = vc->deleted + np;
+    if (np) vc->iters = vc->iters + 1;
     vc->front[par ^ 1u] = 0;          // the next iteration's insert buffer
     vc->n_heavy = 0;
     vc->done = 0;
@@ -270,10 +273,67 @@ struct sssp_s {
     unsigned long long *d_heavy;    // high-degree keys of one iteration
     unsigned long long front_cap;
     Ctr *d_ctr;
-    unsigned long long *h_ring;     // mapped host memory, 2 words per slot
+    unsigned long long *h_ring;     // mapped host memory: (live, stalled) per graph
     unsigned long long *d_ring;
-    cudaEvent_t ev[RING];
+    cudaStream_t cap_stream;        // capture stream
+    cudaEvent_t ev[2];
+    cudaGraphExec_t exec[2];        // UNROLL iterations each, for the graph below
+    Graph key;                      // graph arrays the captured iterations use
+    unsigned long long key_cap;
 };
+
+namespace {
+
+// Enqueues one iteration: deleteMin, relax, relax of the heavy vertices and
+// the insert of the lowered keys.
+int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t par,
+                      uint32_t slot, cudaStream_t st)
+{
+    Ctr *c = s->d_ctr;
+    const unsigned relax_grid =
+        (unsigned)((s->batch + RT - 1) / RT < (uint64_t)s->sm_count * 8 ? (s->batch + RT - 1) / RT
+                                                                         : (uint64_t)s->sm_count * 8);
+    const unsigned heavy_grid = (unsigned)s->sm_count * 4;
+    int rc = heap_delete_min(s->heap, s->d_batch, s->batch, reinterpret_cast<uint64_t *>(&c->popped),
+                             st);
+    if (rc != GHEAP_OK) return rc;
+    sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy);
+    sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy, s->d_ring,
+                                               slot);
+    if (cudaGetLastError() != cudaSuccess) return GHEAP_ERR_CUDA;
+    return heap_insert_dev(s->heap, s->d_front, reinterpret_cast<const uint64_t *>(&c->front[par]),
+                           cap, st);
+}
+
+void drop_graphs(sssp_t s)
+{
+    for (int i = 0; i < 2; i++) {
+        if (s->exec[i]) cudaGraphExecDestroy(s->exec[i]);
+        s->exec[i] = nullptr;
+    }
+}
+
+// Captures graph i: UNROLL iterations that report to ring slot i.
+int capture(sssp_t s, const Graph &g, unsigned long long cap, int i)
+{
+    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    int rc = GHEAP_OK;
+    for (int u = 0; u < UNROLL && rc == GHEAP_OK; u++)
+        rc = enqueue_iteration(s, g, cap, (uint32_t)(u & 1), (uint32_t)i, s->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (rc == GHEAP_OK && e != cudaSuccess) rc = GHEAP_ERR_CUDA;
+    if (rc == GHEAP_OK && cudaGraphInstantiate(&s->exec[i], graph, 0) != cudaSuccess) {
+        s->exec[i] = nullptr;
+        rc = GHEAP_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != GHEAP_OK) cudaGetLastError();
+    return rc;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -281,14 +341,16 @@ int sssp_destroy(sssp_t s)
 {
     if (!s) return GHEAP_ERR_ARG;
     cudaSetDevice(s->device);
+    drop_graphs(s);
     if (s->heap) heap_destroy(s->heap);
     cudaFree(s->d_batch);
     cudaFree(s->d_front);
     cudaFree(s->d_heavy);
     cudaFree(s->d_ctr);
     if (s->h_ring) cudaFreeHost(s->h_ring);
-    for (int i = 0; i < RING; i++)
+    for (int i = 0; i < 2; i++)
         if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     free(s);
     return GHEAP_OK;
 }
@@ -317,13 +379,14 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
               cudaMalloc(&s->d_heavy, (size_t)batch * 8) == cudaSuccess &&
               cudaMalloc(&s->d_ctr, sizeof(Ctr)) == cudaSuccess;
     if (!ok) { sssp_destroy(s); return GHEAP_ERR_OOM; }
-    if (cudaHostAlloc(&s->h_ring, 2 * RING * sizeof(unsigned long long), cudaHostAllocMapped) !=
+    if (cudaHostAlloc(&s->h_ring, 4 * sizeof(unsigned long long), cudaHostAllocMapped) !=
             cudaSuccess ||
-        cudaHostGetDevicePointer(&s->d_ring, s->h_ring, 0) != cudaSuccess) {
+        cudaHostGetDevicePointer(&s->d_ring, s->h_ring, 0) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         sssp_destroy(s);
         return GHEAP_ERR_CUDA;
     }
-    for (int i = 0; i < RING; i++) {
+    for (int i = 0; i < 2; i++) {
         if (cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming) != cudaSuccess) {
             sssp_destroy(s);
             return GHEAP_ERR_CUDA;
@@ -336,6 +399,7 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
 int sssp_set_launch(sssp_t s, uint32_t ctas, uint32_t items_per_thread)
 {
     if (!s) return GHEAP_ERR_ARG;
+    drop_graphs(s);                 // the captured launches carry the old shape
     return heap_set_launch(s->heap, ctas, items_per_thread);
 }
 
@@ -355,6 +419,21 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
     g.col = d_col;
     g.w = d_w;
     g.dist = d_dist;
+    const unsigned long long cap = n_edges ? n_edges : 1;
+
+    // the captured iterations bake in the graph arrays: capture again when
+    // they change
+    const bool same = s->exec[0] && s->exec[1] && s->key.rowptr == g.rowptr && s->key.col == g.col &&
+                      s->key.w == g.w && s->key.dist == g.dist && s->key_cap == cap;
+    if (!same) {
+        drop_graphs(s);
+        for (int i = 0; i < 2; i++) {
+            const int rc = capture(s, g, cap, i);
+            if (rc != GHEAP_OK) { drop_graphs(s); return rc; }
+        }
+        s->key = g;
+        s->key_cap = cap;
+    }
 
     int rc = heap_reset(s->heap, stream);
     if (rc != GHEAP_OK) return rc;
@@ -362,48 +441,24 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
     if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, sizeof(Ctr), st);
     if (e != cudaSuccess) return GHEAP_ERR_CUDA;
     sssp_init<<<1, 1, 0, st>>>(d_dist, source, s->d_front, c);
-    if ((e = cudaGetLastError()) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return GHEAP_ERR_CUDA;
     rc = heap_insert(s->heap, s->d_front, 1, stream);
     if (rc != GHEAP_OK) return rc;
 
-    // relax grids: one chunk of RT popped keys per block, and a grid-wide
-    // spread for the high-degree vertices
-    const unsigned relax_grid =
-        (unsigned)((s->batch + RT - 1) / RT < (uint64_t)s->sm_count * 8 ? (s->batch + RT - 1) / RT
-                                                                         : (uint64_t)s->sm_count * 8);
-    const unsigned heavy_grid = (unsigned)s->sm_count * 4;
-    const unsigned long long cap = n_edges ? n_edges : 1;
-
-    uint64_t issued = 0, ended_at = 0;
+    // two graphs in flight; read the live count one graph behind
     unsigned long long stalled = 0;
-    bool done = false;
-    while (!done) {
-        const uint32_t par = (uint32_t)(issued & 1u), slot = (uint32_t)(issued % RING);
-        rc = heap_delete_min(s->heap, s->d_batch, s->batch, reinterpret_cast<uint64_t *>(&c->popped),
-                             stream);
-        if (rc != GHEAP_OK) return rc;
-        sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy);
-        sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy,
-                                                   s->d_ring, slot);
-        if ((e = cudaGetLastError()) != cudaSuccess) return GHEAP_ERR_CUDA;
-        if (cudaEventRecord(s->ev[slot], st) != cudaSuccess) return GHEAP_ERR_CUDA;
-        rc = heap_insert_dev(s->heap, s->d_front, reinterpret_cast<const uint64_t *>(&c->front[par]),
-                             cap, stream);
-        if (rc != GHEAP_OK) return rc;
-        issued++;
-        // wait for the iteration issued LAG ago and read its live-key count
-        while (issued - ended_at >= (uint64_t)LAG) {
-            const uint32_t js = (uint32_t)(ended_at % RING);
-            if (cudaEventSynchronize(s->ev[js]) != cudaSuccess) return GHEAP_ERR_CUDA;
-            const volatile unsigned long long *r = s->h_ring;
-            const unsigned long long live = r[2 * js];
-            stalled = r[2 * js + 1];
-            ended_at++;
-            if (live == 0 || stalled) {
-                done = true;
-                break;
-            }
-        }
+    for (int i = 0; i < 2; i++) {
+        if (cudaGraphLaunch(s->exec[i], st) != cudaSuccess) return GHEAP_ERR_CUDA;
+        if (cudaEventRecord(s->ev[i], st) != cudaSuccess) return GHEAP_ERR_CUDA;
+    }
+    for (int j = 0;; j ^= 1) {
+        if (cudaEventSynchronize(s->ev[j]) != cudaSuccess) return GHEAP_ERR_CUDA;
+        const volatile unsigned long long *r = s->h_ring;
+        const unsigned long long live = r[2 * j];
+        stalled = r[2 * j + 1];
+        if (live == 0 || stalled) break;
+        if (cudaGraphLaunch(s->exec[j], st) != cudaSuccess) return GHEAP_ERR_CUDA;
+        if (cudaEventRecord(s->ev[j], st) != cudaSuccess) return GHEAP_ERR_CUDA;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) return GHEAP_ERR_CUDA;
     rc = heap_sync(s->heap);
@@ -413,7 +468,7 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
         Ctr hc;
         if (cudaMemcpy(&hc, c, sizeof(Ctr), cudaMemcpyDeviceToHost) != cudaSuccess)
             return GHEAP_ERR_CUDA;
-        stats->iterations = ended_at;
+        stats->iterations = hc.iters;
         stats->keys_deleted = hc.deleted;
         stats->visited = hc.visited;
         stats->edges = hc.edges;
