@@ -72,6 +72,58 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
              uint32_t n_vertices, uint64_t n_edges, uint32_t source, uint32_t *d_dist,
              sssp_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------------
+ * 0/1 knapsack by best-first branch and bound with the heap as the queue of
+ * open search nodes (Section 5.7.2).  Items are sorted by value/weight
+ * descending (exact 64-bit cross products; weightless items first; equal
+ * ratios keep the input order).  A node fixes the first i sorted items and
+ * holds (i, profit, weight) in a node pool; its bound is the floor of the
+ * linear relaxation (Dantzig): the profit, every following item up to the
+ * first that does not fit, and the fitting fraction of that one.  Heap keys
+ * are ((sum of values - bound) << 32) | node id: the largest bound first.
+ * Each iteration deletes `batch` keys, drops those whose bound no longer
+ * beats the incumbent, branches the rest on their next item (take if it
+ * fits, skip), raises the incumbent with leaves and with each child's greedy
+ * completion, and inserts the children whose bound beats the incumbent.  The
+ * search ends when the heap is empty or the best bound left does not beat
+ * the incumbent; the incumbent is then the optimum, the same value a dynamic
+ * program gives.  With gc_threshold > 0, whenever the heap holds more keys
+ * than that (and more than twice what the last pass kept), a filter pass
+ * deletes every key and re-inserts those whose bound still beats the
+ * incumbent (the paper's garbage collection).
+ *
+ * Inputs: w[n], v[n] (uint32_t, device), 1 <= n <= max_items, capacity.
+ * The values must sum below 2^32 - 1 (GHEAP_ERR_ARG otherwise).
+ * ------------------------------------------------------------------------ */
+typedef struct knapsack_s *knapsack_t;
+
+typedef struct {
+    uint64_t best;           /* the optimum total value                     */
+    uint64_t iterations;     /* deleteMin batches that expanded nodes       */
+    uint64_t keys_deleted;   /* keys those batches returned                 */
+    uint64_t explored;       /* nodes branched (bound beat the incumbent)   */
+    uint64_t pruned;         /* popped nodes whose bound no longer did      */
+    uint64_t keys_inserted;  /* children inserted                           */
+    uint64_t nodes;          /* node records allocated                      */
+    uint64_t gc_runs;        /* filter passes                               */
+    uint64_t gc_dropped;     /* keys they removed                           */
+} knapsack_stats;
+
+/* max_items <= 4096.  max_nodes: node records (and heap keys) the search may
+ * allocate, < 2^32 (0 = 2^26).  k, batch: heap node capacity and keys
+ * deleted per iteration.  Allocates 24 bytes per node record (pool and
+ * heap), plus 16 more when gc_threshold > 0.  Errors: ARG, OOM, CUDA. */
+int knapsack_create(knapsack_t *out, uint32_t max_items, uint64_t max_nodes, uint32_t k,
+                    uint32_t batch, uint64_t gc_threshold);
+int knapsack_destroy(knapsack_t s);
+int knapsack_set_launch(knapsack_t s, uint32_t ctas, uint32_t items_per_thread);
+
+/* Solves one instance on `stream` and returns when done (synchronizes).
+ * `stats` (host, may be NULL) receives the optimum and the counters.
+ * Errors: ARG, FULL (more node records than max_nodes), TIMEOUT, STATE, CUDA. */
+int knapsack_run(knapsack_t s, const uint32_t *d_w, const uint32_t *d_v, uint32_t n,
+                 uint32_t capacity, knapsack_stats *stats, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

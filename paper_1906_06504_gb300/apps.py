@@ -8,6 +8,9 @@ from .heap import _check, _stream_ptr, lib
 
 SSSP_STATS_DTYPE = np.dtype([("iterations", "<u8"), ("keys_deleted", "<u8"), ("visited", "<u8"),
                              ("edges", "<u8"), ("keys_inserted", "<u8")])
+KNAPSACK_STATS_DTYPE = np.dtype([(name, "<u8") for name in (
+    "best", "iterations", "keys_deleted", "explored", "pruned", "keys_inserted", "nodes",
+    "gc_runs", "gc_dropped")])
 
 
 class SSSP:
@@ -52,6 +55,53 @@ class SSSP:
     def close(self):
         if self._h is not None:
             lib().sssp_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Knapsack:
+    """0/1 knapsack by best-first branch and bound with the heap as the queue
+    of open nodes (Section 5.7.2)."""
+
+    def __init__(self, max_items, max_nodes=0, k=1024, batch=16384, gc_threshold=0):
+        h = ctypes.c_void_p()
+        _check(lib().knapsack_create(ctypes.byref(h), int(max_items), int(max_nodes), int(k),
+                                     int(batch), int(gc_threshold)), "knapsack_create")
+        self._h = h
+        self.max_items = int(max_items)
+
+    def set_launch(self, ctas=0, items_per_thread=8):
+        _check(lib().knapsack_set_launch(self._h, int(ctas), int(items_per_thread)),
+               "knapsack_set_launch")
+
+    def run(self, w, v, capacity, stream=None):
+        """w, v: int32 CUDA tensors (uint32 bit patterns) of the items.
+        Returns the stats dict; stats["best"] is the optimum value."""
+        for t, name in ((w, "w"), (v, "v")):
+            if not t.is_cuda or not t.is_contiguous() or t.element_size() != 4:
+                raise ValueError("%s must be a contiguous CUDA tensor of 4-byte elements" % name)
+        if w.numel() != v.numel():
+            raise ValueError("w and v differ in length")
+        st = np.zeros(1, dtype=KNAPSACK_STATS_DTYPE)
+        _check(lib().knapsack_run(self._h, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                  w.numel(), int(capacity), ctypes.c_void_p(st.ctypes.data),
+                                  _stream_ptr(stream)), "knapsack_run")
+        return {name: int(st[name][0]) for name in KNAPSACK_STATS_DTYPE.names}
+
+    def close(self):
+        if self._h is not None:
+            lib().knapsack_destroy(self._h)
             self._h = None
 
     def __enter__(self):

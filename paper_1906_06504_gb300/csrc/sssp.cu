@@ -1,31 +1,30 @@
-// apps.cu -- applications of the concurrent heap (arXiv 1906.06504, Section
-// 5.7), written against the public C ABI of gheap.h like any other caller.
+// sssp.cu -- single-source shortest paths on the concurrent heap (arXiv
+// 1906.06504, Section 5.7.1), written against the public C ABI of gheap.h
+// like any other caller.
 //
-// SSSP (Section 5.7.1): the heap holds the active vertices keyed by
-// (distance << 32 | vertex).  One iteration is four stream-ordered steps,
-// none of which returns to the host:
+// The heap holds the active vertices keyed by (distance << 32 | vertex).  One
+// iteration is four stream-ordered steps, none of which returns to the host:
 //   heap_delete_min(batch)  ->  sssp_relax  ->  sssp_relax_heavy  ->  heap_insert_dev
 // sssp_relax drops stale keys and relaxes the out-edges of the others with a
 // block-level load balance (a scan of the degrees, then one edge per thread);
 // vertices of more than HEAVY out-edges are queued for sssp_relax_heavy,
 // which spreads each one over the whole grid.  The last block of
-// sssp_relax_heavy keeps the device's count of live heap keys and writes it
-// to mapped host memory.  The iterations are captured UNROLL at a time in two
-// CUDA graphs that the host launches alternately, reading the count left by
-// one graph while the other runs, so the stream never drains before the heap
-// is empty and the host issues one launch per UNROLL iterations.
+// sssp_relax_heavy keeps the device's count of live heap keys and reports it
+// to the iteration driver of app_loop.cuh.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
+
+#include "app_loop.cuh"
 #include "gheap_apps.h"
 
 namespace {
 
 constexpr int RT = 256;                       // threads of a relax block
 constexpr unsigned long long HEAVY = 2048;    // out-degree spread over the grid
-constexpr int UNROLL = 4;                     // iterations per graph (even: parities alternate)
 constexpr unsigned FULL = 0xffffffffu;
 
 // Device counters of one run.
@@ -273,11 +272,7 @@ struct sssp_s {
     unsigned long long *d_heavy;    // high-degree keys of one iteration
     unsigned long long front_cap;
     Ctr *d_ctr;
-    unsigned long long *h_ring;     // mapped host memory: (live, stalled) per graph
-    unsigned long long *d_ring;
-    cudaStream_t cap_stream;        // capture stream
-    cudaEvent_t ev[2];
-    cudaGraphExec_t exec[2];        // UNROLL iterations each, for the graph below
+    app::Loop loop;
     Graph key;                      // graph arrays the captured iterations use
     unsigned long long key_cap;
 };
@@ -298,39 +293,11 @@ int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t
                              st);
     if (rc != GHEAP_OK) return rc;
     sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy);
-    sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy, s->d_ring,
-                                               slot);
+    sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy,
+                                               s->loop.d_ring, slot);
     if (cudaGetLastError() != cudaSuccess) return GHEAP_ERR_CUDA;
     return heap_insert_dev(s->heap, s->d_front, reinterpret_cast<const uint64_t *>(&c->front[par]),
                            cap, st);
-}
-
-void drop_graphs(sssp_t s)
-{
-    for (int i = 0; i < 2; i++) {
-        if (s->exec[i]) cudaGraphExecDestroy(s->exec[i]);
-        s->exec[i] = nullptr;
-    }
-}
-
-// Captures graph i: UNROLL iterations that report to ring slot i.
-int capture(sssp_t s, const Graph &g, unsigned long long cap, int i)
-{
-    if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return GHEAP_ERR_CUDA;
-    int rc = GHEAP_OK;
-    for (int u = 0; u < UNROLL && rc == GHEAP_OK; u++)
-        rc = enqueue_iteration(s, g, cap, (uint32_t)(u & 1), (uint32_t)i, s->cap_stream);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(s->cap_stream, &graph);
-    if (rc == GHEAP_OK && e != cudaSuccess) rc = GHEAP_ERR_CUDA;
-    if (rc == GHEAP_OK && cudaGraphInstantiate(&s->exec[i], graph, 0) != cudaSuccess) {
-        s->exec[i] = nullptr;
-        rc = GHEAP_ERR_CUDA;
-    }
-    if (graph) cudaGraphDestroy(graph);
-    if (rc != GHEAP_OK) cudaGetLastError();
-    return rc;
 }
 
 }  // namespace
@@ -341,17 +308,13 @@ int sssp_destroy(sssp_t s)
 {
     if (!s) return GHEAP_ERR_ARG;
     cudaSetDevice(s->device);
-    drop_graphs(s);
+    app::loop_free(s->loop);
     if (s->heap) heap_destroy(s->heap);
     cudaFree(s->d_batch);
     cudaFree(s->d_front);
     cudaFree(s->d_heavy);
     cudaFree(s->d_ctr);
-    if (s->h_ring) cudaFreeHost(s->h_ring);
-    for (int i = 0; i < 2; i++)
-        if (s->ev[i]) cudaEventDestroy(s->ev[i]);
-    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-    free(s);
+    delete s;
     return GHEAP_OK;
 }
 
@@ -361,11 +324,11 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
     if (!out) return GHEAP_ERR_ARG;
     *out = nullptr;
     if (n_vertices == 0 || n_vertices == 0xFFFFFFFFu || batch == 0) return GHEAP_ERR_ARG;
-    sssp_t s = (sssp_t)calloc(1, sizeof(sssp_s));
+    sssp_t s = new (std::nothrow) sssp_s();
     if (!s) return GHEAP_ERR_OOM;
-    if (cudaGetDevice(&s->device) != cudaSuccess) { free(s); return GHEAP_ERR_CUDA; }
+    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return GHEAP_ERR_CUDA; }
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) { free(s); return GHEAP_ERR_CUDA; }
+    if (cudaGetDeviceProperties(&prop, s->device) != cudaSuccess) { delete s; return GHEAP_ERR_CUDA; }
     s->sm_count = prop.multiProcessorCount;
     s->n_vertices = n_vertices;
     s->n_edges = n_edges;
@@ -379,19 +342,8 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
               cudaMalloc(&s->d_heavy, (size_t)batch * 8) == cudaSuccess &&
               cudaMalloc(&s->d_ctr, sizeof(Ctr)) == cudaSuccess;
     if (!ok) { sssp_destroy(s); return GHEAP_ERR_OOM; }
-    if (cudaHostAlloc(&s->h_ring, 4 * sizeof(unsigned long long), cudaHostAllocMapped) !=
-            cudaSuccess ||
-        cudaHostGetDevicePointer(&s->d_ring, s->h_ring, 0) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        sssp_destroy(s);
-        return GHEAP_ERR_CUDA;
-    }
-    for (int i = 0; i < 2; i++) {
-        if (cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming) != cudaSuccess) {
-            sssp_destroy(s);
-            return GHEAP_ERR_CUDA;
-        }
-    }
+    rc = app::loop_init(s->loop);
+    if (rc != GHEAP_OK) { sssp_destroy(s); return rc; }
     *out = s;
     return GHEAP_OK;
 }
@@ -399,7 +351,7 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
 int sssp_set_launch(sssp_t s, uint32_t ctas, uint32_t items_per_thread)
 {
     if (!s) return GHEAP_ERR_ARG;
-    drop_graphs(s);                 // the captured launches carry the old shape
+    app::loop_drop(s->loop);        // the captured launches carry the old shape
     return heap_set_launch(s->heap, ctas, items_per_thread);
 }
 
@@ -423,14 +375,13 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
 
     // the captured iterations bake in the graph arrays: capture again when
     // they change
-    const bool same = s->exec[0] && s->exec[1] && s->key.rowptr == g.rowptr && s->key.col == g.col &&
+    const bool same = app::loop_ready(s->loop) && s->key.rowptr == g.rowptr && s->key.col == g.col &&
                       s->key.w == g.w && s->key.dist == g.dist && s->key_cap == cap;
     if (!same) {
-        drop_graphs(s);
-        for (int i = 0; i < 2; i++) {
-            const int rc = capture(s, g, cap, i);
-            if (rc != GHEAP_OK) { drop_graphs(s); return rc; }
-        }
+        const int rc = app::loop_capture(s->loop, [&](uint32_t par, uint32_t slot, cudaStream_t cs) {
+            return enqueue_iteration(s, g, cap, par, slot, cs);
+        });
+        if (rc != GHEAP_OK) return rc;
         s->key = g;
         s->key_cap = cap;
     }
@@ -445,21 +396,10 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
     rc = heap_insert(s->heap, s->d_front, 1, stream);
     if (rc != GHEAP_OK) return rc;
 
-    // two graphs in flight; read the live count one graph behind
     unsigned long long stalled = 0;
-    for (int i = 0; i < 2; i++) {
-        if (cudaGraphLaunch(s->exec[i], st) != cudaSuccess) return GHEAP_ERR_CUDA;
-        if (cudaEventRecord(s->ev[i], st) != cudaSuccess) return GHEAP_ERR_CUDA;
-    }
-    for (int j = 0;; j ^= 1) {
-        if (cudaEventSynchronize(s->ev[j]) != cudaSuccess) return GHEAP_ERR_CUDA;
-        const volatile unsigned long long *r = s->h_ring;
-        const unsigned long long live = r[2 * j];
-        stalled = r[2 * j + 1];
-        if (live == 0 || stalled) break;
-        if (cudaGraphLaunch(s->exec[j], st) != cudaSuccess) return GHEAP_ERR_CUDA;
-        if (cudaEventRecord(s->ev[j], st) != cudaSuccess) return GHEAP_ERR_CUDA;
-    }
+    rc = app::loop_run(s->loop, st, &stalled, [](unsigned long long) { return false; },
+                       [](cudaStream_t) { return GHEAP_OK; });
+    if (rc != GHEAP_OK) return rc;
     if (cudaStreamSynchronize(st) != cudaSuccess) return GHEAP_ERR_CUDA;
     rc = heap_sync(s->heap);
     if (rc != GHEAP_OK) return rc;

@@ -88,6 +88,10 @@ def lib():
             "sssp_destroy": (ctypes.c_int, [vp]),
             "sssp_set_launch": (ctypes.c_int, [vp, u32, u32]),
             "sssp_run": (ctypes.c_int, [vp, vp, vp, vp, u32, u64, u32, vp, vp, vp]),
+            "knapsack_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64, u32, u32, u64]),
+            "knapsack_destroy": (ctypes.c_int, [vp]),
+            "knapsack_set_launch": (ctypes.c_int, [vp, u32, u32]),
+            "knapsack_run": (ctypes.c_int, [vp, vp, vp, u32, u32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
