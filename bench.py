@@ -151,7 +151,7 @@ def run_reference(args):
 
 
 def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, seed_off=0):
-    """SURVEY config 2, mixed part: prefill 2^24 keys, then 2^16 ins-del pairs
+    """Mixed concurrent workload: prefill 2^24 keys, then 2^16 ins-del pairs
     of k keys issued to all blocks at once (Section 5.5 ins-del pairs)."""
     from paper_1906_06504_gb300 import inputs
     from paper_1906_06504_gb300.heap import GHeap, OP_DTYPE, OP_INS, OP_DEL
@@ -187,9 +187,9 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
 
 
 def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
-    """SURVEY config 5, batched part: 256 heaps with log-uniform sizes 2^10 to
-    2^22 keys; one launch inserts all of them, one launch deletes all, both
-    replayed from captured CUDA graphs; k and the merge width autotuned."""
+    """Batched heaps: 256 heaps with log-uniform sizes 2^10 to 2^22 keys; one
+    launch inserts all of them, one launch deletes all, both replayed from
+    captured CUDA graphs; k and the merge width autotuned."""
     from paper_1906_06504_gb300 import inputs, tune as tuner
     from paper_1906_06504_gb300.heap import GHeapSet, OP_INS, OP_DEL
     sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
@@ -240,7 +240,7 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
 
 
 def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256):
-    """SURVEY config 5, served part: Poisson arrivals of insert / deleteMin
+    """Served heaps: Poisson arrivals of insert / deleteMin
     requests of 1..4096 keys over 256 heaps, continuously batched."""
     from paper_1906_06504_gb300 import inputs
     from paper_1906_06504_gb300.serve import HeapServer, latency_summary, poisson_requests
@@ -259,6 +259,213 @@ def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256):
                  "workload": "Poisson arrivals, 1..4096 keys, 50/50 insert/deleteMin, "
                              "256 heaps, k=1024"})
     return summ
+
+
+def _timed(torch, fn, reps=3):
+    """Median wall time (ms) of fn() with the device synchronized around it;
+    fn synchronizes itself (the application runs end when the heap is empty)."""
+    fn()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return float(np.median(ts)), r
+
+
+def run_apps(torch):
+    """The heap as the priority queue of its applications (Section 5.7): SSSP
+    on a 1024x1024 grid and an R-MAT graph (2^20 vertices, 2^23 edges), and
+    best-first knapsack branch and bound (n = 100, 200, strongly correlated).
+    Each result is checked against the oracle (Dijkstra, dynamic program),
+    which is timed on one host core beside it."""
+    import oracle
+    from paper_1906_06504_gb300 import inputs
+    from paper_1906_06504_gb300.apps import SSSP, Knapsack
+    res = {}
+    graphs = [("sssp_grid_1024x1024", inputs.grid_graph(1024, inputs.config_seed(3)), 1024, 1024),
+              ("sssp_rmat_2p20", inputs.rmat_graph(20, 8, inputs.config_seed(3)), 1024, 16384)]
+    for name, g, k, batch in graphs:
+        rowptr, col, w = g
+        t0 = time.perf_counter()
+        want = oracle.dijkstra(*g)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        d = (torch.from_numpy(rowptr.view(np.int64)).cuda(), torch.from_numpy(col.view(np.int32)).cuda(),
+             torch.from_numpy(w.view(np.int32)).cuda())
+        with SSSP(rowptr.size - 1, col.size, k=k, batch=batch) as sp:
+            ms, (dist, st) = _timed(torch, lambda: sp.run(*d))
+        exact = bool(np.array_equal(dist.cpu().numpy().view(np.uint32), want))
+        assert exact
+        keys = st["keys_deleted"] + st["keys_inserted"]
+        res[name] = {"ms": ms, "heap_keys_per_s": keys / (ms / 1e3), "k": k, "batch": batch,
+                     "vertices": int(rowptr.size - 1), "edges": int(col.size), "exact": exact,
+                     "cpu_oracle_ms": cpu_ms, "cpu_oracle": "textbook Dijkstra, binary heap, 1 core",
+                     **st}
+    for n, k, batch in ((100, 1024, 65536), (200, 2048, 16384)):
+        w, v, cap = inputs.knapsack_instance(n, inputs.config_seed(4))
+        t0 = time.perf_counter()
+        want = oracle.knapsack_dp(w, v, cap)
+        cpu_ms = (time.perf_counter() - t0) * 1e3
+        dw = torch.from_numpy(w.view(np.int32)).cuda()
+        dv = torch.from_numpy(v.view(np.int32)).cuda()
+        with Knapsack(n, k=k, batch=batch) as ks:
+            ks.set_launch(items_per_thread=16 if k >= 2048 else 8)
+            ms, st = _timed(torch, lambda: ks.run(dw, dv, cap))
+        assert st["best"] == want
+        keys = st["keys_deleted"] + st["keys_inserted"]
+        res["knapsack_n%d" % n] = {"ms": ms, "heap_keys_per_s": keys / (ms / 1e3), "k": k,
+                                   "batch": batch, "capacity": cap, "exact": True,
+                                   "cpu_oracle_ms": cpu_ms,
+                                   "cpu_oracle": "textbook O(n*C) dynamic program, 1 core", **st}
+    return res
+
+
+# ---------------------------------------------------------------------------
+# parameter sweeps of Section 5 (bench.py --sweep NAME); one JSON line per point
+# ---------------------------------------------------------------------------
+
+def _ev_ms(torch, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _phased(torch, keys, k, ipt, ctas=0):
+    """Insert-only then delete-only of `keys` on a fresh heap; (ins ms, del ms)."""
+    from paper_1906_06504_gb300.heap import GHeap
+    n = keys.numel()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with GHeap(capacity=n, k=k) as h:
+        h.set_launch(ctas=ctas, items_per_thread=ipt)
+        h.insert(keys)                    # warm-up pass
+        h.delete_min(n, out=out, count=cnt)
+        h.sync()
+        ins = _ev_ms(torch, lambda: h.insert(keys))
+        dele = _ev_ms(torch, lambda: h.delete_min(n, out=out, count=cnt))
+        h.sync()
+        assert int(cnt.item()) == n
+    return ins, dele
+
+
+def sweep_k_threads(torch, n=1 << 24):
+    """Node capacity k x block size (Section 5.4): insert-only and delete-only
+    of n uniform keys; the block has 2k/ipt merge threads plus a control warp."""
+    from paper_1906_06504_gb300 import inputs
+    keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n).view(np.int32)).cuda()
+    for k in (64, 128, 256, 512, 1024, 2048):
+        for ipt in (4, 8, 16):
+            threads = max(32, 2 * k // ipt)
+            if threads > (512 if ipt == 4 else 256):
+                continue
+            ins, dele = _phased(torch, keys, k, ipt)
+            yield {"sweep": "k_threads", "k": k, "items_per_thread": ipt,
+                   "threads": threads + 32, "keys": n, "insert_ms": ins, "delete_ms": dele,
+                   "insert_keys_per_s": n / ins * 1e3, "delete_keys_per_s": n / dele * 1e3}
+
+
+def sweep_ctas(torch, n=1 << 26, k=1024, ipt=8):
+    """Thread-block count (Section 5.3): insert-only and delete-only, 2^26 keys."""
+    from paper_1906_06504_gb300 import inputs
+    keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n).view(np.int32)).cuda()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for ctas in (16, 32, 64, 128, sms, 2 * sms, 256, 512):
+        ins, dele = _phased(torch, keys, k, ipt, ctas=ctas)
+        yield {"sweep": "ctas", "ctas": ctas, "k": k, "keys": n, "insert_ms": ins,
+               "delete_ms": dele, "insert_keys_per_s": n / ins * 1e3,
+               "delete_keys_per_s": n / dele * 1e3, "del_over_ins": dele / ins}
+
+
+def sweep_distribution(torch, n=1 << 26, k=1024, ipt=8):
+    """Key order (Section 5.2, Table 1): uniform, ascending, descending; the
+    three hold one multiset, so the deleteMin output must be identical."""
+    from paper_1906_06504_gb300 import inputs
+    from paper_1906_06504_gb300.heap import GHeap
+    first = None
+    for dist in ("uniform", "ascending", "descending"):
+        keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n, dist).view(np.int32)).cuda()
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        with GHeap(capacity=n, k=k) as h:
+            h.set_launch(items_per_thread=ipt)
+            ins = _ev_ms(torch, lambda: h.insert(keys))
+            dele = _ev_ms(torch, lambda: h.delete_min(n, out=out, count=cnt))
+            h.sync()
+        digest = int(out[:: 4096].to(torch.int64).sum().item())
+        same = first is None or (digest == first[0] and torch.equal(out, first[1]))
+        if first is None:
+            first = (digest, out)
+        yield {"sweep": "distribution", "dist": dist, "keys": n, "k": k, "insert_ms": ins,
+               "delete_ms": dele, "total_ms": ins + dele, "same_output_as_uniform": bool(same)}
+
+
+def sweep_partial(torch, n=1 << 24, k=1024, ipt=8):
+    """Partial insert batches (Section 5.6): a fraction f of the INS ops carry
+    a full k-key batch, the others 1..k-1 keys (uniform); same key total."""
+    from paper_1906_06504_gb300 import inputs
+    from paper_1906_06504_gb300.heap import GHeap, OP_DTYPE, OP_INS
+    keys_np = inputs.keys_u32(inputs.config_seed(2) + 300, n)
+    d_keys = torch.from_numpy(keys_np.view(np.int32)).cuda()
+    for f in (0.0, 0.25, 0.5, 0.75, 1.0):
+        rnd = inputs.splitmix64(inputs.config_seed(2) + 301, n // 64 + 16)
+        full = ((rnd >> np.uint64(11)).astype(np.float64) / float(1 << 53)) < f
+        part = (rnd % np.uint64(k - 1) + np.uint64(1)).astype(np.int64)
+        sizes = np.where(full, k, part)
+        cs = np.cumsum(sizes)
+        m = int(np.searchsorted(cs, n)) + 1
+        sizes = sizes[:m].copy()
+        sizes[-1] -= int(cs[m - 1]) - n
+        sizes = sizes[sizes > 0]
+        ops = np.zeros(sizes.size, dtype=OP_DTYPE)
+        ops["kind"] = OP_INS
+        ops["n"] = sizes
+        ops["offset"] = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        d_ops = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        with GHeap(capacity=n, k=k) as h:
+            h.set_launch(items_per_thread=ipt)
+            ms = _ev_ms(torch, lambda: h.ops(d_ops, d_keys, None, max_insert_keys=n))
+            h.sync()
+            assert h.size() == n
+        yield {"sweep": "partial", "full_fraction": f, "ops": int(sizes.size), "keys": n,
+               "insert_ms": ms, "insert_keys_per_s": n / ms * 1e3}
+
+
+def sweep_levels(torch, k=1024, ipt=8, pairs=1 << 14):
+    """Initial heap utilization (Section 5.5): prefill to L full levels, then
+    `pairs` ins-del pairs of k keys from all blocks."""
+    for L in (6, 8, 10, 12, 14, 16, 18):
+        pre = ((1 << L) - 1) * k
+        r = run_mixed(torch, n_prefill=pre, n_pairs=pairs, k=k, ipt=ipt, seed_off=L)
+        yield {"sweep": "levels", "levels": L, "prefill_keys": pre, "pairs": pairs,
+               "ms": r["ms"], "keys_per_s": r["value"]}
+
+
+def sweep_serve(torch, n_requests=20000):
+    """Serving: arrival rate swept up to saturation; p50/p99 latency."""
+    for rate in (10000.0, 25000.0, 50000.0, 100000.0, 200000.0, 400000.0):
+        r = run_serve(torch, n_requests=n_requests, rate=rate)
+        r["sweep"] = "serve_rate"
+        yield r
+
+
+SWEEPS = {"k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
+          "partial": sweep_partial, "levels": sweep_levels, "serve_rate": sweep_serve}
+
+
+def run_sweeps(names):
+    import torch
+    from paper_1906_06504_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    for name in names:
+        for row in SWEEPS[name](torch):
+            print(json.dumps(row), flush=True)
 
 
 def run_gpu(args):
@@ -380,6 +587,7 @@ def run_gpu(args):
         extras["mixed"] = run_mixed(torch, ipt=args.ipt)
         extras["batched"] = run_batched(torch, tune=not args.no_tune)
         extras["serve"] = run_serve(torch)
+        extras["apps"] = run_apps(torch)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -400,6 +608,9 @@ def run_gpu(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clk.summary(),
             "stats_delete": st_del, "stats_insert": st_ins,
+            "root_hold_ns_per_op": {
+                "insert": st_ins["root_hold_ns"] / max(1, st_ins["ins_ops"]),
+                "delete": st_del["root_hold_ns"] / max(1, st_del["del_ops"])},
         }
         line.update(extras)
         if "batched" in extras:
@@ -424,8 +635,13 @@ def main():
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the headline single-heap workload")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--sweep", action="append", choices=sorted(SWEEPS),
+                    help="run a Section 5 parameter sweep instead of the benchmark "
+                         "(one JSON line per point; may repeat)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweeps(args.sweep)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
