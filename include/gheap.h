@@ -85,8 +85,9 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k,
 /* Frees the heap and its device memory (synchronizes the device first). */
 int heap_destroy(gheap_t h);
 
-/* Launch shape of the persistent kernels: `ctas` thread blocks (0 = as many
- * as fit on the device at once), each of 2k/items_per_thread merge threads
+/* Launch shape of the persistent kernels: `ctas` thread blocks (0 = two per
+ * SM, or one where only one fits; a larger count is clamped to the blocks
+ * that fit on the device at once), each of 2k/items_per_thread merge threads
  * (at least 32; at most 512 for items_per_thread 4, 256 for 8 and 16) plus
  * one control warp that takes the node locks; items_per_thread in {4, 8, 16}.
  * The paper's best setting is k = 1024 with 512 threads (Section 5.4), i.e.

@@ -26,7 +26,7 @@ struct gheap_s {
     gheap_log_entry *d_log;
     uint64_t log_cap;
     unsigned long long *d_stats;
-    uint32_t ctas;           // 0 = fill the device
+    uint32_t ctas;           // 0 = two blocks per SM
     uint32_t ipt;            // merge outputs per thread: 2, 4 or 8
     uint64_t timeout_ns;
     int sm_count;
@@ -82,8 +82,13 @@ int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
     if (e != cudaSuccess || per_sm < 1) return GHEAP_ERR_CUDA;
-    uint64_t grid = sp.ctas ? sp.ctas : (uint64_t)per_sm * sp.sm_count;
-    if (grid > (uint64_t)per_sm * sp.sm_count) grid = (uint64_t)per_sm * sp.sm_count;
+    // default: two blocks per SM.  Every operation passes the root lock, and
+    // thousands of small blocks spinning on it (k = 64 fits 32 per SM) turn
+    // each hand-over into a thundering herd; an explicit count is clamped
+    // only by residency
+    const uint64_t resident = (uint64_t)per_sm * sp.sm_count;
+    uint64_t grid = sp.ctas ? sp.ctas : (uint64_t)(per_sm < 2 ? per_sm : 2) * sp.sm_count;
+    if (grid > resident) grid = resident;
     if (grid > n_ops) grid = n_ops;
     if (grid == 0) return GHEAP_OK;
     e = cudaMemsetAsync(sp.d_ctl, 0, sizeof(gh::Ctl), s);
