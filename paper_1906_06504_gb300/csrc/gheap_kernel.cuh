@@ -92,16 +92,23 @@ __host__ __device__ __forceinline__ unsigned long long rw_make(uint32_t m, uint3
     return (unsigned long long)m | ((unsigned long long)s << 32);
 }
 
-// Heap header: the root word (waiters spin on it), the linearization counter
-// (touched only by the root holder) and the sticky error, each on its own
-// 128-byte line.
+// Heap header.  The root lock is a ticket lock: an operation draws `next`,
+// waits until `serving` equals its ticket, and on release stores the root
+// word and then advances `serving`; waiters poll `serving` only, so a release
+// wakes exactly one of them, in arrival order.  The root word (m, s and a
+// held byte that only heap_debug_hold_root sets) shares the line of
+// `serving`; the ticket dispenser, the linearization counter (touched only
+// by the root holder) and the sticky error each have a 128-byte line.
 struct __align__(128) Hdr {
     unsigned long long root;
-    uint32_t _p0[30];
+    unsigned long long serving;
+    uint32_t _p0[28];
     unsigned long long seq;
     uint32_t _p1[30];
     uint32_t err;
     uint32_t _p2[31];
+    unsigned long long next;
+    uint32_t _p3[30];
 };
 
 // Per-launch work distribution, zeroed before every launch.
@@ -209,21 +216,23 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t cas_acquire(uint32_t *p, uint32_t cmp, uint32_t val)
 {
     uint32_t old;
     asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
                  : "=r"(old) : "l"(p), "r"(cmp), "r"(val) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ unsigned long long cas_acquire64(unsigned long long *p,
-                                                            unsigned long long cmp,
-                                                            unsigned long long val)
-{
-    unsigned long long old;
-    asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;"
-                 : "=l"(old) : "l"(p), "l"(cmp), "l"(val) : "memory");
     return old;
 }
 
@@ -251,7 +260,11 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
 template <typename K>
 __device__ __forceinline__ void release_root_word(const HeapView<K> &H, uint32_t m, uint32_t s)
 {
-    st_release64(&H.hdr->root, rw_make(m, s));
+    st_relaxed64(&H.hdr->root, rw_make(m, s));
+    // the release orders the root word and every write the block made before
+    // its barrier ahead of the hand-over to the next ticket
+    const unsigned long long t = ld_relaxed64(&H.hdr->serving);
+    st_release64(&H.hdr->serving, t + 1);
 }
 
 template <typename K>
@@ -299,6 +312,26 @@ __device__ __forceinline__ void lap(Shared &sh, uint32_t i, long long &t)
 // bounded waits (single control lane)
 // ---------------------------------------------------------------------------
 
+// Counts one more poll of a wait; every 8th checks the sticky error and the
+// time bound.  False: give up.
+template <typename K>
+__device__ __forceinline__ bool wait_ok(const Params<K> &p, const HeapView<K> &H,
+                                        unsigned long long &t0, uint32_t &it)
+{
+    ++it;
+    if ((it & 7u) == 0) {
+        if (ld_relaxed(&H.hdr->err) != E_NONE) return false;
+        unsigned long long now = gtimer();
+        if (t0 == 0) {
+            t0 = now;
+        } else if (now - t0 > p.timeout_ns) {
+            atomicCAS(&H.hdr->err, E_NONE, E_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
 template <typename K>
 __device__ __forceinline__ bool keep_waiting(const Params<K> &p, const HeapView<K> &H,
                                              unsigned long long &t0, uint32_t &it)
@@ -330,18 +363,26 @@ template <typename K>
 __device__ bool lock_root(const Params<K> &p, const HeapView<K> &H, Shared &sh,
                           unsigned long long &word)
 {
-    unsigned long long *w = &H.hdr->root;
     unsigned long long t0 = 0;
     uint32_t it = 0;
+    const unsigned long long ticket = atomicAdd(&H.hdr->next, 1ull);
+    for (;;) {
+        const unsigned long long at = ld_acquire64(&H.hdr->serving);
+        if (at == ticket) break;
+        if (!wait_ok(p, H, t0, it)) return false;
+        // the head of the queue polls fast; the others sleep about as long as
+        // the holds ahead of them
+        const unsigned long long ahead = ticket - at;
+        __nanosleep(ahead <= 1 ? 32u : (ahead < 16 ? 256u * (uint32_t)ahead : 4096u));
+    }
+    // our turn; a held byte set by heap_debug_hold_root blocks here too
+    unsigned long long *w = &H.hdr->root;
     for (;;) {
         unsigned long long v = ld_relaxed64(w);
         if ((v >> 56) == 0) {
-            unsigned long long old = cas_acquire64(w, v, v | ROOT_HELD);
-            if (old == v) {
-                if (it) stat_add(sh, STAT_WAITS, 1);
-                word = v;
-                return true;
-            }
+            if (it) stat_add(sh, STAT_WAITS, 1);
+            word = v;
+            return true;
         }
         if (!keep_waiting(p, H, t0, it)) return false;
     }
