@@ -180,7 +180,10 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
         torch.cuda.synchronize()
         h.sync()
         ms = e0.elapsed_time(e1)
-        assert h.size() == n_prefill
+        # DELs may overtake INSs on a small heap and return fewer than k keys:
+        # check conservation instead of a fixed final size
+        c = counts.cpu().numpy().astype(np.int64)
+        assert h.size() == n_prefill + int(c[0::2].sum()) - int(c[1::2].sum())
     moved = int(counts.sum().item())
     return {"workload": "prefill 2^24, then 2^16 ins-del pairs of k=1024 keys, all blocks",
             "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}

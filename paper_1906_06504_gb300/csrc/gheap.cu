@@ -39,6 +39,9 @@ namespace {
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? GHEAP_OK : GHEAP_ERR_CUDA; }
 
+// heap_debug_hold_root: holds the root's ticket lock forever.
+__global__ void take_root_ticket(gh::Hdr *hdr) { atomicAdd(&hdr->next, 1ull); }
+
 int map_dev_err(uint32_t e)
 {
     switch (e) {
@@ -887,9 +890,9 @@ int heap_debug_hold_root(gheap_t h, void *stream)
 {
     if (!h) return GHEAP_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
-    // a nonzero top byte is "held"
-    return cuda_err(cudaMemsetAsync(&h->d_hdr->root, 0x01, sizeof(unsigned long long),
-                                    (cudaStream_t)stream));
+    // draw the root's next ticket and never release it
+    take_root_ticket<<<1, 1, 0, (cudaStream_t)stream>>>(h->d_hdr);
+    return cuda_err(cudaGetLastError());
 }
 
 int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n)

@@ -79,30 +79,39 @@ enum : uint32_t {
     N_STATS = 20
 };
 
-// Root word: bits 0-31 m (full nodes), bits 32-47 s (partial-buffer keys),
-// a nonzero top byte = held.
-constexpr unsigned long long ROOT_HELD = 1ull << 56;
-__host__ __device__ __forceinline__ uint32_t rw_m(unsigned long long v) { return (uint32_t)v; }
+// Root word: bits 0-29 m (full nodes), bits 30-41 s (partial-buffer keys),
+// bits 42-63 the turn of the root's ticket lock.  The lock holder stores
+// (m, s, turn + 1) in one release, so the next ticket learns that it holds
+// the root and reads (m, s) with the same load.
+constexpr uint32_t RW_TURN_BITS = 22;
+constexpr unsigned long long RW_TURN_MASK = (1ull << RW_TURN_BITS) - 1;
+__host__ __device__ __forceinline__ uint32_t rw_m(unsigned long long v)
+{
+    return (uint32_t)v & ((1u << 30) - 1u);
+}
 __host__ __device__ __forceinline__ uint32_t rw_s(unsigned long long v)
 {
-    return (uint32_t)(v >> 32) & 0xFFFFu;
+    return (uint32_t)(v >> 30) & 0xFFFu;
 }
-__host__ __device__ __forceinline__ unsigned long long rw_make(uint32_t m, uint32_t s)
+__host__ __device__ __forceinline__ uint32_t rw_turn(unsigned long long v)
 {
-    return (unsigned long long)m | ((unsigned long long)s << 32);
+    return (uint32_t)(v >> 42);
+}
+__host__ __device__ __forceinline__ unsigned long long rw_make(uint32_t m, uint32_t s, uint32_t turn)
+{
+    return (unsigned long long)m | ((unsigned long long)s << 30) |
+           ((unsigned long long)(turn & RW_TURN_MASK) << 42);
 }
 
-// Heap header.  The root lock is a ticket lock: an operation draws `next`,
-// waits until `serving` equals its ticket, and on release stores the root
-// word and then advances `serving`; waiters poll `serving` only, so a release
-// wakes exactly one of them, in arrival order.  The root word (m, s and a
-// held byte that only heap_debug_hold_root sets) shares the line of
-// `serving`; the ticket dispenser, the linearization counter (touched only
-// by the root holder) and the sticky error each have a 128-byte line.
+// Heap header.  The root lock is a ticket lock: an operation draws a ticket
+// from `next` and waits until the root word's turn equals it (modulo 2^22,
+// far more than the blocks that can wait at once); waiters poll the root
+// word only, so a release wakes exactly one of them, in arrival order.  The
+// ticket dispenser, the linearization counter (touched only by the root
+// holder) and the sticky error each have a 128-byte line.
 struct __align__(128) Hdr {
     unsigned long long root;
-    unsigned long long serving;
-    uint32_t _p0[28];
+    uint32_t _p0[30];
     unsigned long long seq;
     uint32_t _p1[30];
     uint32_t err;
@@ -165,6 +174,7 @@ struct Shared {
     unsigned long long out_off;
     unsigned long long t_root;
     uint32_t m, s, take, tslot;
+    uint32_t turn;            // root ticket held by this block
     int stop;
     int abort;
     int deliver;
@@ -223,11 +233,6 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     return v;
 }
 
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
-}
-
 __device__ __forceinline__ uint32_t cas_acquire(uint32_t *p, uint32_t cmp, uint32_t val)
 {
     uint32_t old;
@@ -258,15 +263,13 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
 // (the barrier + single release-store hand-off used between thread blocks by
 // split-K GEMM epilogues).
 template <typename K>
-__device__ __forceinline__ void release_root_word(const HeapView<K> &H, uint32_t m, uint32_t s)
+__device__ __forceinline__ void release_root_word(const HeapView<K> &H, const Shared &sh,
+                                                  uint32_t m, uint32_t s)
 {
-    st_relaxed64(&H.hdr->root, rw_make(m, s));
-    // the release orders the root word and every write the block made before
-    // its barrier ahead of the hand-over to the next ticket
-    const unsigned long long t = ld_relaxed64(&H.hdr->serving);
-    st_release64(&H.hdr->serving, t + 1);
+    // the release orders every write the block made before its barrier ahead
+    // of the hand-over to the next ticket
+    st_release64(&H.hdr->root, rw_make(m, s, sh.turn + 1));
 }
-
 template <typename K>
 __device__ __forceinline__ K kmax() { return ~K(0); }
 
@@ -365,26 +368,20 @@ __device__ bool lock_root(const Params<K> &p, const HeapView<K> &H, Shared &sh,
 {
     unsigned long long t0 = 0;
     uint32_t it = 0;
-    const unsigned long long ticket = atomicAdd(&H.hdr->next, 1ull);
+    const uint32_t ticket = (uint32_t)(atomicAdd(&H.hdr->next, 1ull) & RW_TURN_MASK);
     for (;;) {
-        const unsigned long long at = ld_acquire64(&H.hdr->serving);
-        if (at == ticket) break;
-        if (!wait_ok(p, H, t0, it)) return false;
-        // the head of the queue polls fast; the others sleep about as long as
-        // the holds ahead of them
-        const unsigned long long ahead = ticket - at;
-        __nanosleep(ahead <= 1 ? 32u : (ahead < 16 ? 256u * (uint32_t)ahead : 4096u));
-    }
-    // our turn; a held byte set by heap_debug_hold_root blocks here too
-    unsigned long long *w = &H.hdr->root;
-    for (;;) {
-        unsigned long long v = ld_relaxed64(w);
-        if ((v >> 56) == 0) {
+        const unsigned long long v = ld_acquire64(&H.hdr->root);
+        const uint32_t ahead = (ticket - rw_turn(v)) & (uint32_t)RW_TURN_MASK;
+        if (ahead == 0) {
             if (it) stat_add(sh, STAT_WAITS, 1);
+            sh.turn = ticket;
             word = v;
             return true;
         }
-        if (!keep_waiting(p, H, t0, it)) return false;
+        if (!wait_ok(p, H, t0, it)) return false;
+        // the head of the queue polls fast; the others sleep about as long as
+        // the holds ahead of them
+        __nanosleep(ahead <= 1 ? 32u : (ahead < 16 ? 256u * ahead : 4096u));
     }
 }
 
@@ -867,8 +864,8 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         bar_all();
         if (ctrl && lane == 0) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            if (fits) release_root_word(H, m, n + s);
-            else release_root_word(H, 1u, n < k ? n + s - k : s);
+            if (fits) release_root_word(H, sh, m, n + s);
+            else release_root_word(H, sh, 1u, n < k ? n + s - k : s);
         }
         return true;
     }
@@ -974,7 +971,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         if (ctrl && lane == 0) {
             if (cur_w == nullptr) {
                 stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                release_root_word(H, tslot, s);
+                release_root_word(H, sh, tslot, s);
             } else {
                 st_release(cur_w, ST_AVAIL);
             }
@@ -1114,7 +1111,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         bar_all();
         if (ctrl && lane == 0) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root_word(H, 0u, s - take);
+            release_root_word(H, sh, 0u, s - take);
         }
         return true;
     }
@@ -1189,7 +1186,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     if (root_gone) {
         if (ctrl && lane == 0) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root_word(H, 0u, tn);
+            release_root_word(H, sh, 0u, tn);
         }
         return true;
     }
@@ -1272,7 +1269,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     long long tr = clock64();
                     if (at_root) {
                         stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                        release_root_word(H, nm, ns);
+                        release_root_word(H, sh, nm, ns);
                     } else {
                         st_release(cur_w, ST_AVAIL);
                     }
@@ -1402,7 +1399,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 long long tr = clock64();
                 if (at_root) {
                     stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                    release_root_word(H, nm, ns);
+                    release_root_word(H, sh, nm, ns);
                 } else {
                     st_release(cur_w, ST_AVAIL);
                 }
@@ -1433,7 +1430,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     if (ctrl && lane == 0) {
         if (cur_w == nullptr) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root_word(H, nm, ns);
+            release_root_word(H, sh, nm, ns);
         } else {
             st_release(cur_w, ST_AVAIL);
         }
