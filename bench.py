@@ -598,7 +598,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
                        "keys": n, "k": k, "threads_per_block": 2 * k // args.ipt,
-                       "ctas": args.ctas or "two per SM",
+                       "ctas": args.ctas or "one per SM",
                        "l2": "inputs and heap (256 MB each) exceed the 126 MB L2",
                        "insert_ms": ins_avg_ms, "delete_ms": del_avg_ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

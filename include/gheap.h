@@ -85,9 +85,9 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k,
 /* Frees the heap and its device memory (synchronizes the device first). */
 int heap_destroy(gheap_t h);
 
-/* Launch shape of the persistent kernels: `ctas` thread blocks (0 = two per
- * SM, or one where only one fits; a larger count is clamped to the blocks
- * that fit on the device at once), each of 2k/items_per_thread merge threads
+/* Launch shape of the persistent kernels: `ctas` thread blocks (0 = one per
+ * SM; a larger count is clamped to the blocks that fit on the device at
+ * once), each of 2k/items_per_thread merge threads
  * (at least 32; at most 512 for items_per_thread 4, 256 for 8 and 16) plus
  * one control warp that takes the node locks; items_per_thread in {4, 8, 16}.
  * The paper's best setting is k = 1024 with 512 threads (Section 5.4), i.e.
@@ -234,7 +234,9 @@ int heapset_bind(gheapset_t s, uint32_t i, gheap_t h, void *stream);
  * heap goes back to its owner. */
 int heapset_unbind(gheapset_t s, uint32_t i, void *stream);
 
-/* Launch shape and wait bound, as heap_set_launch / heap_set_timeout. */
+/* Launch shape and wait bound, as heap_set_launch / heap_set_timeout, except
+ * that ctas = 0 means two blocks per SM (operations on different heaps run
+ * in parallel). */
 int heapset_set_launch(gheapset_t s, uint32_t ctas, uint32_t items_per_thread);
 int heapset_set_timeout(gheapset_t s, uint64_t ns);
 

@@ -26,7 +26,7 @@ struct gheap_s {
     gheap_log_entry *d_log;
     uint64_t log_cap;
     unsigned long long *d_stats;
-    uint32_t ctas;           // 0 = two blocks per SM
+    uint32_t ctas;           // 0 = one block per SM
     uint32_t ipt;            // merge outputs per thread: 2, 4 or 8
     uint64_t timeout_ns;
     int sm_count;
@@ -66,9 +66,11 @@ uint32_t threads_for(uint32_t k, uint32_t ipt) { return merge_threads_for(k, ipt
 // Merge threads allowed by the kernel's launch bound for this merge width.
 uint32_t max_merge_threads(uint32_t ipt) { return ipt >= 8 ? 256 : 512; }
 
-// What a launch needs besides the kernel parameters.
+// What a launch needs besides the kernel parameters.  `per_sm_default`:
+// blocks per SM when ctas is 0.
 struct Shape {
     uint32_t k, ipt, ctas;
+    uint32_t per_sm_default = 1;
     int sm_count;
     gh::Ctl *d_ctl;
 };
@@ -85,12 +87,13 @@ int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, smem);
     if (e != cudaSuccess || per_sm < 1) return GHEAP_ERR_CUDA;
-    // default: two blocks per SM.  Every operation passes the root lock, and
-    // thousands of small blocks spinning on it (k = 64 fits 32 per SM) turn
-    // each hand-over into a thundering herd; an explicit count is clamped
-    // only by residency
+    // default: one block per SM on a single heap, whose operations all pass
+    // its root lock (more blocks only add waiters: measured flat to slightly
+    // slower from 16 to 512 blocks at k = 1024), two on a heap set; an
+    // explicit count is clamped only by residency
     const uint64_t resident = (uint64_t)per_sm * sp.sm_count;
-    uint64_t grid = sp.ctas ? sp.ctas : (uint64_t)(per_sm < 2 ? per_sm : 2) * sp.sm_count;
+    const uint32_t dflt = per_sm < (int)sp.per_sm_default ? (uint32_t)per_sm : sp.per_sm_default;
+    uint64_t grid = sp.ctas ? sp.ctas : (uint64_t)dflt * sp.sm_count;
     if (grid > resident) grid = resident;
     if (grid > n_ops) grid = n_ops;
     if (grid == 0) return GHEAP_OK;
@@ -532,6 +535,7 @@ int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void 
     sp.k = S->k;
     sp.ipt = S->ipt;
     sp.ctas = S->ctas;
+    sp.per_sm_default = 2;
     sp.sm_count = S->sm_count;
     sp.d_ctl = S->d_ctl;
     return launch_k<K>(sp, p, n_ops, st);
