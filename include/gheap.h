@@ -48,6 +48,13 @@ typedef struct gheap_s *gheap_t;
 
 /* heap_create flags */
 #define GHEAP_FLAG_STATS 1u    /* count node loads/stores and merges       */
+#define GHEAP_FLAG_BOTTOM_UP 2u /* heap_insert / heap_insert_dev insert
+    bottom-up (BU-INS, Sections 3.2.2 and 3.3.4): a full batch is placed at
+    the target node and rises, merging with each parent (which keeps the k
+    smallest), until the parent's maximum is at most the batch's minimum or
+    the root is reached; it holds the root only to reserve the target.  An
+    insert is linearized under its last lock.  Launches that mix inserts and
+    deletes (heap_ops, heap sets) still insert top-down.                    */
 
 /* One entry of the linearization record (Section 3.3.3): the operation that
  * held the root lock in that position.  kind_n = (kind << 24) | n with kind

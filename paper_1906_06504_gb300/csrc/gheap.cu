@@ -142,6 +142,7 @@ gh::Params<K> base_params(gheap_t h, uint32_t mode)
     p.k = h->k;
     p.timeout_ns = h->timeout_ns;
     p.mode = mode;
+    p.bu = (h->flags & GHEAP_FLAG_BOTTOM_UP) ? 1u : 0u;
     p.call_id = ++h->call_id;
     return p;
 }

@@ -50,8 +50,15 @@ namespace gh {
 // DELIVERED: the INS wrote its keys for the DEL that marked the slot.
 enum : uint32_t {
     ST_EMPTY = 0, ST_AVAIL = 1, ST_INUSE = 2, ST_TARGET = 3, ST_MARKED = 4,
-    ST_DELIVERED = 5
+    ST_DELIVERED = 5, ST_INSHOLD = 6
 };
+// INSHOLD (bottom-up insert, Section 3.3.4): the node holds the keys of an
+// insert still on its way up, released while that insert waits for the
+// parent.  The word is ST_INSHOLD | owner << 8, owner naming the insert.
+__host__ __device__ __forceinline__ uint32_t inshold(uint32_t owner)
+{
+    return ST_INSHOLD | (owner << 8);
+}
 constexpr uint32_t ST_GAVE_UP = ~0u;
 constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
@@ -149,7 +156,7 @@ struct Params {
     uint32_t k;
     uint32_t mode;
     uint32_t call_id;
-    uint32_t _pad;
+    uint32_t bu;                 // MODE_INSERT: bottom-up inserts (Section 3.3.4)
     unsigned long long timeout_ns;
     const K *in;                 // MODE_INSERT / MODE_OPS input keys
     K *out;                      // MODE_DELETE / MODE_OPS output keys
@@ -740,8 +747,9 @@ template <typename K>
 __device__ __forceinline__ void take_ticket(const Params<K> &p, const HeapView<K> &H, Shared &sh,
                                             uint32_t kind, uint32_t n, unsigned long long ref)
 {
-    unsigned long long seq = __ldcg(&H.hdr->seq);
-    __stcg(&H.hdr->seq, seq + 1);
+    // atomic: a bottom-up insert takes its number under its last lock, which
+    // need not be the root's
+    const unsigned long long seq = atomicAdd(&H.hdr->seq, 1ull);
     sh.seq = seq;
     if (seq < H.log_cap) {
         gheap_log_entry e;
@@ -756,11 +764,18 @@ __device__ __forceinline__ void take_ticket(const Params<K> &p, const HeapView<K
 // INS (Section 3.2.2 top-down INS, Section 3.3.2 partial buffer)
 // ---------------------------------------------------------------------------
 
+template <typename K, int IPT>
+__device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
+                        uint32_t tslot, uint32_t s, uint32_t n, unsigned long long ref);
+
 // The batch PB(0)[0..n) is sorted (PB(0)[n..k) hold the key maximum) and the
 // block has met on a barrier since.  Buffers: 0 = the carried batch, 1 and 2
 // = the current and the next node, 3 = the partial buffer.  Returns false
-// when the operation had to give up (the block must stop).
-template <typename K, int IPT>
+// when the operation had to give up (the block must stop).  BU: a full batch
+// is placed at its target and rises (bottom-up INS, Section 3.2.2) instead
+// of walking down from the root; the root step and the partial buffer are
+// the same.
+template <typename K, int IPT, bool BU>
 __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t n, unsigned long long ref)
 {
@@ -785,22 +800,24 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 const uint32_t m = rw_m(w), s = rw_s(w);
                 sh.m = m;
                 sh.s = s;
-                take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
                 const bool full = n == k || n + s >= k;
+                // a bottom-up batch that leaves the root level is linearized
+                // under its last lock instead
+                if (!(BU && full && m >= 1)) take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
                 if (full && m >= 1) {
                     if (m + 1 > H.max_nodes) {
                         set_err(H, E_FULL);
                         sh.abort = 1;
                     } else {
                         sh.tslot = m + 1;
-                        st_relaxed(&H.state[m + 1], ST_TARGET);
+                        st_relaxed(&H.state[m + 1], BU ? ST_INUSE : ST_TARGET);
                     }
                 }
             }
         }
         __syncwarp();
         const uint32_t tslot = sh.tslot;
-        if (tslot) {
+        if (!BU && tslot) {
             g2s(base + (size_t)k, root, k, lane, 32u);   // root -> buffer 1
             cp_async_commit();
             if (lane == 0) {
@@ -886,6 +903,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         s = n + s - k;
     }
+    if (BU) return bu_rise<K, IPT>(p, H, sh, base, tslot, s, n, ref);
 
     uint32_t ib = 1, ic = 2;       // current node, next node
     K *cur_keys = root;
@@ -1003,6 +1021,143 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         cur_keys = nkeys;
         cur_w = nw;
         par ^= 1;
+    }
+}
+
+// Bottom-up INS (Sections 3.2.2 and 3.3.4) of a full batch A = PB(0) whose
+// target slot `tslot` the root step reserved (state INUSE, held by this
+// block); `s` is the partial buffer size to publish.  The root is released
+// at once, the batch is stored at the target, and then, level by level:
+// lock the parent (waiting while it is in use or holds another insert's
+// batch), take the own node back from INSHOLD, stop when parent max <= batch
+// min (early stop, Section 4.3), else MergeAndSort(parent, batch): the
+// parent keeps the k smallest, which rise on, and the node keeps the k
+// largest.  Between levels the node is released as INSHOLD; the operation
+// is linearized under its last lock (the early-stop pair or the root).
+// Locks are only ever requested while holding nothing but the own INSHOLD
+// node, which no other operation takes, so the upward walk cannot deadlock
+// with the top-down locking of other inserts.  This path runs in insert-only
+// launches: a DEL never meets an INSHOLD node.
+template <typename K, int IPT>
+__device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
+                        uint32_t tslot, uint32_t s, uint32_t n, unsigned long long ref)
+{
+    const uint32_t k = p.k;
+    const bool ctrl = is_ctrl();
+    const uint32_t lane = clane();
+    K *const A = base;                        // the rising batch
+    K *const P = base + (size_t)k;            // the parent's keys
+    const uint32_t me = inshold((uint32_t)(sh.op & 0xFFFFFFull));
+
+    // publish the new node count and the buffer, release the root, store the
+    // batch at the target and hand the target over as INSHOLD
+    bar_all();
+    if (ctrl && lane == 0) {
+        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+        release_root_word(H, sh, tslot, s);
+    }
+    if (!ctrl) {
+        s2g(H.keys + (size_t)tslot * k, A, k);
+        if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+    }
+    bar_all();
+    if (ctrl && lane == 0) st_release(&H.state[tslot], me);
+
+    uint32_t cslot = tslot, cnode = slot_node(tslot);
+    for (;;) {
+        const uint32_t pnode = cnode >> 1;
+        const bool proot = pnode == 1;
+        const uint32_t pslot = slot_node(pnode);     // the map is its own inverse
+        K *pkeys = H.keys + (size_t)pslot * k;
+        uint32_t *pw = &H.state[pslot];
+        if (ctrl) {
+            long long tw = clock64();
+            if (lane == 0) {
+                if (proot) {
+                    unsigned long long w = 0;
+                    sh.abort = !lock_root(p, H, sh, w);
+                    sh.m = rw_m(w);
+                    sh.s = rw_s(w);
+                    sh.t_root = gtimer();
+                } else {
+                    unsigned long long t0 = 0;
+                    uint32_t it = 0;
+                    for (;;) {
+                        const uint32_t v = ld_relaxed(pw);
+                        if (v == ST_AVAIL && try_lock(pw) == ST_AVAIL) break;
+                        if (v != ST_AVAIL && v != ST_INUSE && (v & 0xFFu) != ST_INSHOLD) {
+                            set_err(H, E_STATE);
+                            sh.abort = 1;
+                            break;
+                        }
+                        if (!keep_waiting(p, H, t0, it)) {
+                            sh.abort = 1;
+                            break;
+                        }
+                    }
+                    if (it) stat_add(sh, STAT_WAITS, 1);
+                }
+                if (!sh.abort && atomicCAS(&H.state[cslot], me, ST_INUSE) != me) {
+                    set_err(H, E_STATE);
+                    sh.abort = 1;
+                }
+                lap(sh, STAT_INS_WAIT_CYC, tw);
+                stat_add(sh, STAT_INS_LEVELS, 1);
+            }
+            __syncwarp();
+            if (!sh.abort) {
+                g2s(P, pkeys, k, lane, 32u);
+                cp_async_commit();
+                cp_async_wait();
+            }
+        }
+        bar_all();
+        if (sh.abort) return false;
+        if (!ctrl) {
+            long long tm = clock64();
+            const K pmax = P[k - 1], amin = A[0];
+            bar_mg();
+            if (pmax <= amin) {
+                if (threadIdx.x == 0) {
+                    sh.halt = 1;
+                    stat_add(sh, STAT_SKIPS, 1);
+                }
+            } else {
+                // MergeAndSort(parent, batch): the k smallest rise with the
+                // parent, the k largest stay in the node
+                merge_kk<K, IPT>(P, A, A, P, k);
+                s2g(H.keys + (size_t)cslot * k, P, k);
+                s2g(pkeys, A, k);
+                if (threadIdx.x == 0) {
+                    sh.halt = 0;
+                    stat_add(sh, STAT_MERGES, 1);
+                    stat_add(sh, STAT_STORES, 2);
+                }
+            }
+            if (threadIdx.x == 0) {
+                stat_add(sh, STAT_LOADS, 1);
+                lap(sh, STAT_INS_STEP_CYC, tm);
+            }
+        }
+        bar_all();
+        const bool done = sh.halt || proot;
+        if (ctrl && lane == 0) {
+            if (done) take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
+            st_release(&H.state[cslot], ST_AVAIL);
+            if (proot) {
+                stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                release_root_word(H, sh, sh.m, sh.s);
+            } else {
+                st_release(pw, done ? ST_AVAIL : me);
+            }
+        }
+        if (done) {
+            bar_all();
+            if (threadIdx.x == 0) sh.halt = 0;
+            return true;
+        }
+        cslot = pslot;
+        cnode = pnode;
     }
 }
 
@@ -1550,7 +1705,9 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
                 if (threadIdx.x == 0) lap(sh, STAT_INS_SORT_CYC, ts);
             }
             bar_all();
-            ok = ins_op<K, IPT>(p, H, sh, base, n, listed ? op : off);
+            ok = (p.bu && p.mode == MODE_INSERT)
+                     ? ins_op<K, IPT, true>(p, H, sh, base, n, listed ? op : off)
+                     : ins_op<K, IPT, false>(p, H, sh, base, n, listed ? op : off);
             if (threadIdx.x == 0) {
                 stat_add(sh, STAT_INS, 1);
                 if (listed && p.out_counts) p.out_counts[op] = ok ? n : 0u;

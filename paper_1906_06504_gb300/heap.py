@@ -16,6 +16,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_FULL, ERR_TIMEOUT, ERR_CUDA, ERR_STATE, ERR_TOO_LARGE = (
     -1, -2, -3, -4, -5, -6, -7)
 FLAG_STATS = 1
+FLAG_BOTTOM_UP = 2
 OP_INS, OP_DEL = 1, 2
 SET_CURSOR = 1 << 23
 
@@ -120,13 +121,15 @@ def slot_to_node(j):
 class GHeap:
     """A generalized concurrent heap in device memory (include/gheap.h)."""
 
-    def __init__(self, capacity, k=1024, key_bytes=4, log_capacity=0, stats=False, _handle=None):
+    def __init__(self, capacity, k=1024, key_bytes=4, log_capacity=0, stats=False,
+                 bottom_up=False, _handle=None):
         L = lib()
         self._owned = _handle is None
         if _handle is None:
             h = ctypes.c_void_p()
+            flags = (FLAG_STATS if stats else 0) | (FLAG_BOTTOM_UP if bottom_up else 0)
             _check(L.heap_create(ctypes.byref(h), int(capacity), int(k), int(key_bytes),
-                                 FLAG_STATS if stats else 0, int(log_capacity)), "heap_create")
+                                 flags, int(log_capacity)), "heap_create")
         else:
             h = ctypes.c_void_p(_handle)
         self._h = h
