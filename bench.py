@@ -278,6 +278,22 @@ def _timed(torch, fn, reps=3):
     return float(np.median(ts)), r
 
 
+def run_bottom_up(torch, n=N_KEYS, k=K, ipt=8, steps=3):
+    """The headline workload with bottom-up inserts (BU-INS/TD-DEL heap,
+    Section 3.3.4): insert-all bottom-up, then deleteMin-all."""
+    from paper_1906_06504_gb300 import inputs
+    keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n).view(np.int32)).cuda()
+    ins, dele = [], []
+    for _ in range(steps):
+        a, b = _phased(torch, keys, k, ipt, bottom_up=True)
+        ins.append(a)
+        dele.append(b)
+    ins_ms, del_ms = float(np.median(ins)), float(np.median(dele))
+    return {"workload": "insert-all (bottom-up) + deleteMin-all, 2^26 uniform u32, k=1024",
+            "value": 2.0 * n / ((ins_ms + del_ms) / 1e3), "unit": UNIT,
+            "insert_ms": ins_ms, "delete_ms": del_ms}
+
+
 def run_apps(torch):
     """The heap as the priority queue of its applications (Section 5.7): SSSP
     on a 1024x1024 grid and an R-MAT graph (2^20 vertices, 2^23 edges), and
@@ -339,13 +355,13 @@ def _ev_ms(torch, fn):
     return e0.elapsed_time(e1)
 
 
-def _phased(torch, keys, k, ipt, ctas=0):
+def _phased(torch, keys, k, ipt, ctas=0, bottom_up=False):
     """Insert-only then delete-only of `keys` on a fresh heap; (ins ms, del ms)."""
     from paper_1906_06504_gb300.heap import GHeap
     n = keys.numel()
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    with GHeap(capacity=n, k=k) as h:
+    with GHeap(capacity=n, k=k, bottom_up=bottom_up) as h:
         h.set_launch(ctas=ctas, items_per_thread=ipt)
         h.insert(keys)                    # warm-up pass
         h.delete_min(n, out=out, count=cnt)
@@ -386,26 +402,30 @@ def sweep_ctas(torch, n=1 << 26, k=1024, ipt=8):
 
 
 def sweep_distribution(torch, n=1 << 26, k=1024, ipt=8):
-    """Key order (Section 5.2, Table 1): uniform, ascending, descending; the
-    three hold one multiset, so the deleteMin output must be identical."""
+    """Key order x insert variant (Section 5.2, Table 1): uniform, ascending,
+    descending keys, top-down and bottom-up inserts; all six runs hold one
+    multiset, so the deleteMin output must be identical."""
     from paper_1906_06504_gb300 import inputs
     from paper_1906_06504_gb300.heap import GHeap
     first = None
-    for dist in ("uniform", "ascending", "descending"):
-        keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n, dist).view(np.int32)).cuda()
-        out = torch.empty(n, dtype=torch.int32, device="cuda")
-        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        with GHeap(capacity=n, k=k) as h:
-            h.set_launch(items_per_thread=ipt)
-            ins = _ev_ms(torch, lambda: h.insert(keys))
-            dele = _ev_ms(torch, lambda: h.delete_min(n, out=out, count=cnt))
-            h.sync()
-        digest = int(out[:: 4096].to(torch.int64).sum().item())
-        same = first is None or (digest == first[0] and torch.equal(out, first[1]))
-        if first is None:
-            first = (digest, out)
-        yield {"sweep": "distribution", "dist": dist, "keys": n, "k": k, "insert_ms": ins,
-               "delete_ms": dele, "total_ms": ins + dele, "same_output_as_uniform": bool(same)}
+    for variant in ("top-down", "bottom-up"):
+        for dist in ("uniform", "ascending", "descending"):
+            keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n, dist)
+                                    .view(np.int32)).cuda()
+            out = torch.empty(n, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            with GHeap(capacity=n, k=k, bottom_up=variant == "bottom-up") as h:
+                h.set_launch(items_per_thread=ipt)
+                ins = _ev_ms(torch, lambda: h.insert(keys))
+                dele = _ev_ms(torch, lambda: h.delete_min(n, out=out, count=cnt))
+                h.sync()
+            same = first is None or bool(torch.equal(out, first))
+            if first is None:
+                first = out
+            yield {"sweep": "distribution", "insert": variant, "dist": dist, "keys": n, "k": k,
+                   "insert_ms": ins, "delete_ms": dele, "total_ms": ins + dele,
+                   "same_output_as_first": same}
+            del keys
 
 
 def sweep_partial(torch, n=1 << 24, k=1024, ipt=8):
@@ -457,7 +477,13 @@ def sweep_serve(torch, n_requests=20000):
         yield r
 
 
-SWEEPS = {"k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
+def sweep_apps(torch):
+    """The application workloads alone (one line each), e.g. for a profile."""
+    for name, r in run_apps(torch).items():
+        yield {"sweep": "apps", "app": name, **r}
+
+
+SWEEPS = {"apps": sweep_apps, "k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
           "partial": sweep_partial, "levels": sweep_levels, "serve_rate": sweep_serve}
 
 
@@ -590,6 +616,7 @@ def run_gpu(args):
         extras["mixed"] = run_mixed(torch, ipt=args.ipt)
         extras["batched"] = run_batched(torch, tune=not args.no_tune)
         extras["serve"] = run_serve(torch)
+        extras["bottom_up"] = run_bottom_up(torch, ipt=args.ipt)
         extras["apps"] = run_apps(torch)
     if rank == 0:
         line = {
