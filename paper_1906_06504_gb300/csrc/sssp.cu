@@ -288,7 +288,7 @@ int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t
     const unsigned relax_grid =
         (unsigned)((s->batch + RT - 1) / RT < (uint64_t)s->sm_count * 8 ? (s->batch + RT - 1) / RT
                                                                          : (uint64_t)s->sm_count * 8);
-    const unsigned heavy_grid = (unsigned)s->sm_count * 4;
+    const unsigned heavy_grid = (unsigned)s->sm_count;   // usually no heavy vertex: keep it cheap
     int rc = heap_delete_min(s->heap, s->d_batch, s->batch, reinterpret_cast<uint64_t *>(&c->popped),
                              st);
     if (rc != GHEAP_OK) return rc;
