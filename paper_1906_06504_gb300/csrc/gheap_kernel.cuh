@@ -1385,10 +1385,9 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         if (ctrl && lane == 0) stat_add(sh, STAT_DEL_LEVELS, 1);
         bar_all();   // everybody has read the decision inputs
         const bool at_root = cur_w == nullptr;
-        // the next DEL waits on this DEL's level-1 node rather than on the
-        // root, so the next level is prefetched during the merges at every
-        // level, the root included
-        const bool defer = false;
+        // the next level's locks and loads run on the control warp during the
+        // merges at every level, the root included; the current node is
+        // released by merge thread 0 as soon as its keys are stored
 
         if (pl != pr) {
             // one child present (the other is absent or an INS target)
@@ -1408,19 +1407,13 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 long long tm = clock64();
                 merge_kk<K, IPT>(Bc, X, Bc, X, k);
                 s2g(cur_keys, Bc, k);
+                // the node is final: release it as soon as the merge threads'
+                // stores are done, not after the next level's locks
+                bar_mg();
                 if (threadIdx.x == 0) {
                     stat_add(sh, STAT_MERGES, 1);
                     stat_add(sh, STAT_STORES, 1);
                     lap(sh, STAT_DEL_MERGE_CYC, tm);
-                }
-            } else if (!defer) {
-                long long tw = clock64();
-                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
-                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
-            }
-            bar_all();
-            if (ctrl) {
-                if (lane == 0) {
                     long long tr = clock64();
                     if (at_root) {
                         stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
@@ -1430,15 +1423,12 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     }
                     lap(sh, STAT_DEL_REL_CYC, tr);
                 }
-                __syncwarp();
-                if (defer) {
-                    long long tw = clock64();
-                    cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
-                                     sh.lk[par ^ 1]);
-                    if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
-                }
+            } else {
+                long long tw = clock64();
+                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
+                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
             }
-            if (defer) bar_all();
+            bar_all();
             const uint32_t xb = usel ? il : ir, ob = usel ? ir : il;
             const uint32_t n1 = ic, n2 = ob;
             ic = xb; il = f1; ir = f2; f1 = n1; f2 = n2;
@@ -1499,7 +1489,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 sh.halt = cmax <= S[0];
                 lap(sh, STAT_DEL_MERGE_CYC, tm);
             }
-        } else if (!defer && lane < 2) {
+        } else if (lane < 2) {
             // try the small child's children while the merge threads work
             const uint32_t gx = lane ? gr : gl;
             if (gx) t_try = try_lock(&H.state[gx]);
@@ -1512,7 +1502,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 st_release(big_w, ST_AVAIL);
                 lap(sh, STAT_DEL_REL_CYC, tr);
             }
-            if (!defer) {
+            {
                 if (halt) {
                     // the sift ends here: give back what the tries took
                     if (lane < 2 && t_try == ST_AVAIL)
@@ -1537,9 +1527,21 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 // MergeAndSort(cur, small child): cur keeps the k smallest
                 merge_kk<K, IPT>(Bc, S, Bc, S, k);
                 s2g(cur_keys, Bc, k);
+                // the node is final: release it as soon as the merge threads'
+                // stores are done, while the control warp may still wait for
+                // the next level's locks
+                bar_mg();
                 if (threadIdx.x == 0) {
                     stat_add(sh, STAT_MERGES, 1);
                     stat_add(sh, STAT_STORES, 1);
+                    long long tr = clock64();
+                    if (at_root) {
+                        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                        release_root_word(H, sh, nm, ns);
+                    } else {
+                        st_release(cur_w, ST_AVAIL);
+                    }
+                    lap(sh, STAT_DEL_REL_CYC, tr);
                 }
             }
             if (threadIdx.x == 0) lap(sh, STAT_DEL_MERGE_CYC, tm);
@@ -1549,25 +1551,6 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             if (ctrl && lane == 0) st_release(sm_w, ST_AVAIL);
             break;
         }
-        if (ctrl) {
-            if (lane == 0) {
-                long long tr = clock64();
-                if (at_root) {
-                    stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                    release_root_word(H, sh, nm, ns);
-                } else {
-                    st_release(cur_w, ST_AVAIL);
-                }
-                lap(sh, STAT_DEL_REL_CYC, tr);
-            }
-            __syncwarp();
-            if (defer) {
-                long long tw = clock64();
-                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
-                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
-            }
-        }
-        if (defer) bar_all();
         const uint32_t sb = S_is_C ? il : ir, lb = S_is_C ? ir : il;
         const uint32_t n1 = ic, n2 = lb;
         ic = sb; il = f1; ir = f2; f1 = n1; f2 = n2;
