@@ -186,6 +186,7 @@ struct Shared {
     int abort;
     int deliver;
     int halt;                 // DEL: the sift ends after MergeAndSort(l, r)
+    int swap;                 // DEL: MergeAndSort(cur, small child) is a swap
     uint32_t lk[2][2];        // lock results, double-buffered by level
     unsigned long long cnt[N_STATS];
 };
@@ -1487,6 +1488,9 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             }
             if (threadIdx.x == 0) {
                 sh.halt = cmax <= S[0];
+                // every carried key above the small half: the second
+                // MergeAndSort is a swap (Section 4.3)
+                sh.swap = Bc[0] >= S[k - 1];
                 lap(sh, STAT_DEL_MERGE_CYC, tm);
             }
         } else if (lane < 2) {
@@ -1496,6 +1500,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         bar_all();
         const bool halt = sh.halt;
+        const bool swap2 = !halt && sh.swap;
         if (ctrl) {
             if (lane == 0) {
                 long long tr = clock64();
@@ -1524,15 +1529,21 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
                 }
             } else {
-                // MergeAndSort(cur, small child): cur keeps the k smallest
-                merge_kk<K, IPT>(Bc, S, Bc, S, k);
-                s2g(cur_keys, Bc, k);
+                // MergeAndSort(cur, small child): cur keeps the k smallest;
+                // with disjoint ranges cur takes the small half as it is and
+                // the carried keys go on down unchanged
+                if (swap2) {
+                    s2g(cur_keys, S, k);
+                } else {
+                    merge_kk<K, IPT>(Bc, S, Bc, S, k);
+                    s2g(cur_keys, Bc, k);
+                }
                 // the node is final: release it as soon as the merge threads'
                 // stores are done, while the control warp may still wait for
                 // the next level's locks
                 bar_mg();
                 if (threadIdx.x == 0) {
-                    stat_add(sh, STAT_MERGES, 1);
+                    stat_add(sh, swap2 ? STAT_SKIPS : STAT_MERGES, 1);
                     stat_add(sh, STAT_STORES, 1);
                     long long tr = clock64();
                     if (at_root) {
@@ -1551,8 +1562,15 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             if (ctrl && lane == 0) st_release(sm_w, ST_AVAIL);
             break;
         }
-        const uint32_t sb = S_is_C ? il : ir, lb = S_is_C ? ir : il;
-        const uint32_t n1 = ic, n2 = lb;
+        uint32_t sb = S_is_C ? il : ir;
+        const uint32_t lb = S_is_C ? ir : il;
+        uint32_t n1 = ic;
+        if (swap2) {
+            // the carried keys (still in the current buffer) are the small
+            // child's new contents
+            const uint32_t t = sb; sb = n1; n1 = t;
+        }
+        const uint32_t n2 = lb;
         ic = sb; il = f1; ir = f2; f1 = n1; f2 = n2;
         node = smn;
         cur_keys = sm_keys;
