@@ -35,6 +35,33 @@ METRIC = "insert+deleteMin keys/s (k=1024, 2^26 u32)"
 UNIT = "keys/s"
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
+# launch (2^26 u32 keys, k=1024, one block per SM), from one ncu capture of
+# the kernel built from sources with these SHA-256 digests; reported as null
+# once the sources differ.
+MEASURED_TRAFFIC = {
+    "sources": {
+        "gheap_kernel.cuh": "6097cb7355c91a9c410498ab8002dd2bc4d9d51cc4dfb0017c1c03705c5ebfbc",
+        "gheap.cu": "485133b6a7f12a0ca49973a8b47aee580e70430e5d651c79c4a2bc1775028dbb",
+    },
+    "insert": 710087936 + 745558784,
+    "delete": 1168293888 + 1429215232,
+}
+
+
+def measured_traffic(kind, n, k, ctas):
+    """DRAM bytes of one `kind` launch if the capture applies to this run."""
+    import hashlib
+    if n != N_KEYS or k != K or ctas not in (0, None):
+        return None
+    csrc = os.path.join(ROOT, "paper_1906_06504_gb300", "csrc")
+    for name, digest in MEASURED_TRAFFIC["sources"].items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return MEASURED_TRAFFIC[kind]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -629,7 +656,10 @@ def run_gpu(args):
                        "l2": "inputs and heap (256 MB each) exceed the 126 MB L2",
                        "insert_ms": ins_avg_ms, "delete_ms": del_avg_ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": measured_traffic(dom, n, k, args.ctas)
+                         if args.ipt == 8 else None,
+                         "peak_kind": peak_kind,
                          "kernel": "heap_kernel (%s-all launch)" % dom,
                          "algorithmic_bytes": dom_bytes},
             "cpu_baseline": cpu,
