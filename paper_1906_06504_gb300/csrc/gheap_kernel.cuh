@@ -60,6 +60,9 @@ __host__ __device__ __forceinline__ uint32_t inshold(uint32_t owner)
     return ST_INSHOLD | (owner << 8);
 }
 constexpr uint32_t ST_GAVE_UP = ~0u;
+// How often a DEL hands the root back rather than wait, holding it, for an
+// INS still on its way to the last node.
+constexpr uint32_t DEL_YIELDS = 64;
 constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
 enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2, MODE_SET = 3 };
@@ -1216,7 +1219,31 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     // ---- take the root, the ticket and the output range
     if (ctrl && lane == 0) {
         unsigned long long w = 0;
-        sh.abort = !lock_root(p, H, sh, w);
+        // A DEL that would refill the root from a last node still owed by an
+        // INS in flight (TARGET) would hold the root for that whole delivery.
+        // Before it has done anything visible it hands the root back and
+        // queues again (a bounded number of times), so that the operations
+        // behind it proceed meanwhile; after that it waits as before.
+        for (uint32_t yields = 0;; ++yields) {
+            sh.abort = !lock_root(p, H, sh, w);
+            if (sh.abort) break;
+            const uint32_t m = rw_m(w), s = rw_s(w);
+            uint32_t w_now = want;
+            if (p.mode == MODE_DELETE) {
+                const unsigned long long done = p.ctl->delivered;
+                const unsigned long long rem = p.n > done ? p.n - done : 0ull;
+                w_now = rem < want ? (uint32_t)rem : want;
+            }
+            const uint32_t t_now = w_now < (m >= 1 ? k : s) ? w_now : (m >= 1 ? k : s);
+            if (yields < DEL_YIELDS && s < t_now && m >= 2 &&
+                ld_relaxed(&H.state[m]) == ST_TARGET) {
+                release_root_word(H, sh, m, s);
+                stat_add(sh, STAT_WAITS, 1);
+                __nanosleep(512);
+                continue;
+            }
+            break;
+        }
         lap(sh, STAT_DEL_ACQ_CYC, tp);
         if (!sh.abort) {
             sh.t_root = gtimer();
