@@ -630,6 +630,64 @@ __device__ __forceinline__ void ld_run(const K *p, K (&v)[N])
     }
 }
 
+// ld_run / st_run of a run wider than 16 bytes per thread, with the 16-byte
+// chunks taken in a per-thread rotated order: thread t starts at chunk
+// (t >> (3 - log2 C)) mod C, so that the 8 threads of a quarter warp cover
+// 8 distinct groups of 4 banks (without the rotation, runs of 32 bytes give
+// a 2-way and runs of 64 bytes a 4-way bank conflict).  The merge uses it
+// for 32-byte runs, where the rotation is a swap of two registers.
+template <typename K, int N>
+__device__ __forceinline__ void ld_run_rot(const K *p, K (&v)[N])
+{
+    constexpr int C = (int)sizeof(K) * N / 16;          // chunks per thread
+    constexpr int PER = 16 / (int)sizeof(K);
+    static_assert(C == 2 || C == 4 || C == 8, "run of 2, 4 or 8 chunks");
+    constexpr int SH = C == 2 ? 2 : (C == 4 ? 1 : 0);
+    const int r = (int)(threadIdx.x >> SH) & (C - 1);
+    uint4 t[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) t[i] = reinterpret_cast<const uint4 *>(p)[(i + r) & (C - 1)];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        // chunk j was loaded by instruction (j - r) mod C
+        uint4 x = t[0];
+#pragma unroll
+        for (int i = 1; i < C; ++i)
+            if (((j - r) & (C - 1)) == i) x = t[i];
+        union { uint4 u; K k[PER]; } q;
+        q.u = x;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) v[j * PER + e] = q.k[e];
+    }
+}
+
+template <typename K, int N>
+__device__ __forceinline__ void st_run_rot(K *p, const K (&v)[N])
+{
+    constexpr int C = (int)sizeof(K) * N / 16;
+    constexpr int PER = 16 / (int)sizeof(K);
+    static_assert(C == 2 || C == 4 || C == 8, "run of 2, 4 or 8 chunks");
+    constexpr int SH = C == 2 ? 2 : (C == 4 ? 1 : 0);
+    const int r = (int)(threadIdx.x >> SH) & (C - 1);
+    uint4 t[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        union { uint4 u; K k[PER]; } q;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) q.k[e] = v[j * PER + e];
+        t[j] = q.u;
+    }
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        // instruction i stores chunk (i + r) mod C
+        uint4 x = t[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j)
+            if (((i + r) & (C - 1)) == j) x = t[j];
+        reinterpret_cast<uint4 *>(p)[(i + r) & (C - 1)] = x;
+    }
+}
+
 template <typename K, int N>
 __device__ __forceinline__ void st_run(K *p, const K (&v)[N])
 {
@@ -708,7 +766,8 @@ __device__ __noinline__ void merge_full(const K *a, const K *b, K *dlo, K *dhi, 
         bar_mg();
     }
     K v[IPT];
-    ld_run<K, IPT>(d + u * IPT, v);
+    if constexpr (sizeof(K) * IPT == 32) ld_run_rot<K, IPT>(d + u * IPT, v);
+    else ld_run<K, IPT>(d + u * IPT, v);
     const uint32_t lane = tid & 31u;
 #pragma unroll
     for (uint32_t lm = 16; lm >= 1; lm >>= 1) {
@@ -732,7 +791,8 @@ __device__ __noinline__ void merge_full(const K *a, const K *b, K *dlo, K *dhi, 
             }
         }
     }
-    st_run<K, IPT>(d + u * IPT, v);
+    if constexpr (sizeof(K) * IPT == 32) st_run_rot<K, IPT>(d + u * IPT, v);
+    else st_run<K, IPT>(d + u * IPT, v);
     bar_mg();
 }
 
