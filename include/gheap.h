@@ -151,7 +151,8 @@ int heap_reset(gheap_t h, void *stream);
 
 /* Copies up to `cap` linearization-record entries to host memory, in root
  * order, and the total number of operations recorded so far to *n_total
- * (synchronizes).  Entries beyond log_capacity are not kept. */
+ * (synchronizes).  Entries beyond log_capacity are not kept; a heap created
+ * with log_capacity 0 keeps no record and counts nothing (*n_total = 0). */
 int heap_get_log(gheap_t h, gheap_log_entry *host_buf, uint64_t cap,
                  uint64_t *n_copied, uint64_t *n_total);
 

@@ -811,6 +811,12 @@ template <typename K>
 __device__ __forceinline__ void take_ticket(const Params<K> &p, const HeapView<K> &H, Shared &sh,
                                             uint32_t kind, uint32_t n, unsigned long long ref)
 {
+    // no record kept: no number to draw (it would cost a round trip to L2
+    // inside the root hold)
+    if (H.log_cap == 0) {
+        sh.seq = 0;
+        return;
+    }
     // atomic: a bottom-up insert takes its number under its last lock, which
     // need not be the root's
     const unsigned long long seq = atomicAdd(&H.hdr->seq, 1ull);
@@ -1278,7 +1284,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
 
     // ---- take the root, the ticket and the output range
     if (ctrl && lane == 0) {
-        unsigned long long w = 0;
+        unsigned long long w = 0, done = 0;
         // A DEL that would refill the root from a last node still owed by an
         // INS in flight (TARGET) would hold the root for that whole delivery.
         // Before it has done anything visible it hands the root back and
@@ -1288,15 +1294,18 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             sh.abort = !lock_root(p, H, sh, w);
             if (sh.abort) break;
             const uint32_t m = rw_m(w), s = rw_s(w);
+            // both loads go out before either value is used; a delete-only
+            // launch has no insert in flight (earlier launches completed)
+            const uint32_t last_state =
+                (p.mode != MODE_DELETE && m >= 2) ? ld_relaxed(&H.state[m]) : ST_AVAIL;
+            if (p.mode == MODE_DELETE) done = ld_relaxed64(&p.ctl->delivered);
             uint32_t w_now = want;
             if (p.mode == MODE_DELETE) {
-                const unsigned long long done = p.ctl->delivered;
                 const unsigned long long rem = p.n > done ? p.n - done : 0ull;
                 w_now = rem < want ? (uint32_t)rem : want;
             }
             const uint32_t t_now = w_now < (m >= 1 ? k : s) ? w_now : (m >= 1 ? k : s);
-            if (yields < DEL_YIELDS && s < t_now && m >= 2 &&
-                ld_relaxed(&H.state[m]) == ST_TARGET) {
+            if (yields < DEL_YIELDS && s < t_now && m >= 2 && last_state == ST_TARGET) {
                 release_root_word(H, sh, m, s);
                 stat_add(sh, STAT_WAITS, 1);
                 __nanosleep(512);
@@ -1311,8 +1320,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             sh.m = m;
             sh.s = s;
             if (p.mode == MODE_DELETE) {
-                unsigned long long done = p.ctl->delivered;
-                unsigned long long rem = p.n > done ? p.n - done : 0ull;
+                const unsigned long long rem = p.n > done ? p.n - done : 0ull;
                 want = rem < want ? (uint32_t)rem : want;
                 out_off = done;
             } else if (req >= 0) {
