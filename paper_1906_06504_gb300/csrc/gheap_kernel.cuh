@@ -185,6 +185,7 @@ struct Shared {
     unsigned long long t_root;
     uint32_t m, s, take, tslot;
     uint32_t turn;            // root ticket held by this block
+    int lockfree;             // bottom-up INS: target reserved without the root lock
     int stop;
     int abort;
     int deliver;
@@ -273,6 +274,21 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
 // thread has observed, so a block that acquires the word sees all of them
 // (the barrier + single release-store hand-off used between thread blocks by
 // split-K GEMM epilogues).
+// Release for launches in which full bottom-up batches reserve their target
+// slots without the lock (an atomic add on m): the holder adds its own
+// changes of m and s and the turn increment in one atomic, so that the
+// concurrent reservations are kept.  Fields cannot carry into each other:
+// m < 2^30 and 0 <= s + ds < 2^12 throughout.
+template <typename K>
+__device__ __forceinline__ void release_root_delta(const HeapView<K> &H, int dm, int ds)
+{
+    const unsigned long long d = (unsigned long long)(long long)dm +
+                                 (unsigned long long)(long long)ds * (1ull << 30) +
+                                 (1ull << 42);
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(&H.hdr->root), "l"(d)
+                 : "memory");
+}
+
 template <typename K>
 __device__ __forceinline__ void release_root_word(const HeapView<K> &H, const Shared &sh,
                                                   uint32_t m, uint32_t s)
@@ -836,7 +852,7 @@ __device__ __forceinline__ void take_ticket(const Params<K> &p, const HeapView<K
 
 template <typename K, int IPT>
 __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
-                        uint32_t tslot, uint32_t s, uint32_t n, unsigned long long ref);
+                        uint32_t tslot, bool locked, int ds, uint32_t n, unsigned long long ref);
 
 // The batch PB(0)[0..n) is sorted (PB(0)[n..k) hold the key maximum) and the
 // block has met on a barrier since.  Buffers: 0 = the carried batch, 1 and 2
@@ -861,26 +877,50 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     // the root and try the first node of the path
     if (ctrl) {
         if (lane == 0) {
-            unsigned long long w = 0;
-            sh.abort = !lock_root(p, H, sh, w);
-            lap(sh, STAT_INS_ACQ_CYC, tp);
             sh.tslot = 0;
-            if (!sh.abort) {
-                sh.t_root = gtimer();
-                const uint32_t m = rw_m(w), s = rw_s(w);
-                sh.m = m;
-                sh.s = s;
-                const bool full = n == k || n + s >= k;
-                // a bottom-up batch that leaves the root level is linearized
-                // under its last lock instead
-                if (!(BU && full && m >= 1)) take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
-                if (full && m >= 1) {
-                    if (m + 1 > H.max_nodes) {
-                        set_err(H, E_FULL);
-                        sh.abort = 1;
-                    } else {
-                        sh.tslot = m + 1;
-                        st_relaxed(&H.state[m + 1], BU ? ST_INUSE : ST_TARGET);
+            sh.lockfree = 0;
+            if (BU && n == k && rw_m(ld_relaxed64(&H.hdr->root)) >= 1) {
+                // a full bottom-up batch touches neither the root nor the
+                // buffer: it reserves its target with an atomic add on m and
+                // never takes the root lock here (m only grows during an
+                // insert launch, and no DEL runs in one)
+                const unsigned long long old = atomicAdd(&H.hdr->root, 1ull);
+                const uint32_t slot = rw_m(old) + 1;
+                sh.m = rw_m(old);
+                sh.s = rw_s(old);
+                sh.lockfree = 1;
+                if (slot > H.max_nodes) {
+                    set_err(H, E_FULL);
+                    sh.abort = 1;
+                } else {
+                    sh.tslot = slot;
+                    st_relaxed(&H.state[slot], ST_INUSE);
+                }
+            } else {
+                unsigned long long w = 0;
+                sh.abort = !lock_root(p, H, sh, w);
+                lap(sh, STAT_INS_ACQ_CYC, tp);
+                if (!sh.abort) {
+                    sh.t_root = gtimer();
+                    const uint32_t m = rw_m(w), s = rw_s(w);
+                    sh.m = m;
+                    sh.s = s;
+                    const bool full = n == k || n + s >= k;
+                    // a bottom-up batch that leaves the root level is
+                    // linearized under its last lock instead
+                    if (!(BU && full && m >= 1)) take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
+                    if (full && m >= 1) {
+                        // bottom-up: the slot comes from the same atomic add
+                        // as the unlocked reservations
+                        const uint32_t slot =
+                            BU ? rw_m(atomicAdd(&H.hdr->root, 1ull)) + 1 : m + 1;
+                        if (slot > H.max_nodes) {
+                            set_err(H, E_FULL);
+                            sh.abort = 1;
+                        } else {
+                            sh.tslot = slot;
+                            st_relaxed(&H.state[slot], BU ? ST_INUSE : ST_TARGET);
+                        }
                     }
                 }
             }
@@ -951,8 +991,13 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         bar_all();
         if (ctrl && lane == 0) {
             stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            if (fits) release_root_word(H, sh, m, n + s);
-            else release_root_word(H, sh, 1u, n < k ? n + s - k : s);
+            if (BU) {
+                if (fits) release_root_delta(H, 0, (int)n);
+                else release_root_delta(H, 1, (n < k ? (int)(n + s - k) : (int)s) - (int)s);
+            } else {
+                if (fits) release_root_word(H, sh, m, n + s);
+                else release_root_word(H, sh, 1u, n < k ? n + s - k : s);
+            }
         }
         return true;
     }
@@ -973,7 +1018,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         s = n + s - k;
     }
-    if (BU) return bu_rise<K, IPT>(p, H, sh, base, tslot, s, n, ref);
+    if (BU) return bu_rise<K, IPT>(p, H, sh, base, tslot, !sh.lockfree, (int)s - (int)sh.s, n, ref);
 
     uint32_t ib = 1, ic = 2;       // current node, next node
     K *cur_keys = root;
@@ -1095,22 +1140,25 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
 }
 
 // Bottom-up INS (Sections 3.2.2 and 3.3.4) of a full batch A = PB(0) whose
-// target slot `tslot` the root step reserved (state INUSE, held by this
-// block); `s` is the partial buffer size to publish.  The root is released
-// at once, the batch is stored at the target, and then, level by level:
-// lock the parent (waiting while it is in use or holds another insert's
-// batch), take the own node back from INSHOLD, stop when parent max <= batch
-// min (early stop, Section 4.3), else MergeAndSort(parent, batch): the
-// parent keeps the k smallest, which rise on, and the node keeps the k
-// largest.  Between levels the node is released as INSHOLD; the operation
-// is linearized under its last lock (the early-stop pair or the root).
-// Locks are only ever requested while holding nothing but the own INSHOLD
-// node, which no other operation takes, so the upward walk cannot deadlock
-// with the top-down locking of other inserts.  This path runs in insert-only
-// launches: a DEL never meets an INSHOLD node.
+// target slot `tslot` is reserved (state INUSE, held by this block).  When
+// the reservation took the root lock (`locked`: a partial batch that
+// overflowed the buffer, or the heap's first node), the root is released
+// first, publishing the buffer-size change `ds`; a full batch on a non-empty
+// heap reserved its slot without the lock.  The batch is stored at the
+// target, and then, level by level: lock the parent (waiting while it is in
+// use or holds another insert's batch), take the own node back from
+// INSHOLD, stop when parent max <= batch min (early stop, Section 4.3), else
+// MergeAndSort(parent, batch): the parent keeps the k smallest, which rise
+// on, and the node keeps the k largest.  Between levels the node is
+// released as INSHOLD; the operation is linearized under its last lock (the
+// early-stop pair or the root).  Locks are only ever requested while
+// holding nothing but the own INSHOLD node, which no other operation takes,
+// so the upward walk cannot deadlock with the top-down locking of other
+// inserts.  This path runs in insert-only launches: a DEL never meets an
+// INSHOLD node, and m only grows.
 template <typename K, int IPT>
 __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
-                        uint32_t tslot, uint32_t s, uint32_t n, unsigned long long ref)
+                        uint32_t tslot, bool locked, int ds, uint32_t n, unsigned long long ref)
 {
     const uint32_t k = p.k;
     const bool ctrl = is_ctrl();
@@ -1119,12 +1167,12 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
     K *const P = base + (size_t)k;            // the parent's keys
     const uint32_t me = inshold((uint32_t)(sh.op & 0xFFFFFFull));
 
-    // publish the new node count and the buffer, release the root, store the
-    // batch at the target and hand the target over as INSHOLD
+    // publish the buffer and release the root (when the reservation took
+    // it), store the batch at the target and hand the target over as INSHOLD
     bar_all();
-    if (ctrl && lane == 0) {
+    if (ctrl && lane == 0 && locked) {
         stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-        release_root_word(H, sh, tslot, s);
+        release_root_delta(H, 0, ds);
     }
     if (!ctrl) {
         s2g(H.keys + (size_t)tslot * k, A, k);
@@ -1216,7 +1264,7 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
             st_release(&H.state[cslot], ST_AVAIL);
             if (proot) {
                 stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                release_root_word(H, sh, sh.m, sh.s);
+                release_root_delta(H, 0, 0);
             } else {
                 st_release(pw, done ? ST_AVAIL : me);
             }
