@@ -3,7 +3,10 @@
 Workload (one step): the raw heap throughput configuration of arXiv 1906.06504
 Section 5.2 at GB300 scale -- 2^26 uniform uint32 keys, node capacity k = 1024,
 inserted into an empty heap and then all deleted (insert-all, deleteMin-all),
-every thread block of the device running operations concurrently.
+every thread block of the device running operations concurrently, on the
+paper's BU-INS/TD-DEL heap (Section 3.3.4: bottom-up inserts, top-down
+deleteMin).  --top-down runs it on the TD-INS/TD-DEL heap instead; the
+JSON line reports the other variant beside the headline.
 
 value  : (keys inserted + keys deleted) / device time, inputs resident in HBM.
 e2e    : the same through the C ABI from pinned host buffers, the H2D copy of
@@ -44,15 +47,16 @@ MEASURED_TRAFFIC = {
         "gheap_kernel.cuh": "6097cb7355c91a9c410498ab8002dd2bc4d9d51cc4dfb0017c1c03705c5ebfbc",
         "gheap.cu": "485133b6a7f12a0ca49973a8b47aee580e70430e5d651c79c4a2bc1775028dbb",
     },
+    "bottom_up": False,
     "insert": 710087936 + 745558784,
     "delete": 1168293888 + 1429215232,
 }
 
 
-def measured_traffic(kind, n, k, ctas):
+def measured_traffic(kind, n, k, ctas, bottom_up):
     """DRAM bytes of one `kind` launch if the capture applies to this run."""
     import hashlib
-    if n != N_KEYS or k != K or ctas not in (0, None):
+    if n != N_KEYS or k != K or ctas not in (0, None) or bottom_up != MEASURED_TRAFFIC["bottom_up"]:
         return None
     csrc = os.path.join(ROOT, "paper_1906_06504_gb300", "csrc")
     for name, digest in MEASURED_TRAFFIC["sources"].items():
@@ -305,18 +309,20 @@ def _timed(torch, fn, reps=3):
     return float(np.median(ts)), r
 
 
-def run_bottom_up(torch, n=N_KEYS, k=K, ipt=8, steps=3):
-    """The headline workload with bottom-up inserts (BU-INS/TD-DEL heap,
-    Section 3.3.4): insert-all bottom-up, then deleteMin-all."""
+def run_variant(torch, bottom_up, n=N_KEYS, k=K, ipt=8, steps=3):
+    """The headline workload on the other heap variant of the paper: insert-all
+    (top-down or bottom-up, Sections 3.3.1 / 3.3.4), then deleteMin-all."""
     from paper_1906_06504_gb300 import inputs
     keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n).view(np.int32)).cuda()
     ins, dele = [], []
     for _ in range(steps):
-        a, b = _phased(torch, keys, k, ipt, bottom_up=True)
+        a, b = _phased(torch, keys, k, ipt, bottom_up=bottom_up)
         ins.append(a)
         dele.append(b)
     ins_ms, del_ms = float(np.median(ins)), float(np.median(dele))
-    return {"workload": "insert-all (bottom-up) + deleteMin-all, 2^26 uniform u32, k=1024",
+    name = "bottom-up" if bottom_up else "top-down"
+    return {"workload": "insert-all (%s) + deleteMin-all, 2^26 uniform u32, k=1024" % name,
+            "heap": "BU-INS/TD-DEL" if bottom_up else "TD-INS/TD-DEL",
             "value": 2.0 * n / ((ins_ms + del_ms) / 1e3), "unit": UNIT,
             "insert_ms": ins_ms, "delete_ms": del_ms}
 
@@ -546,7 +552,8 @@ def run_gpu(args):
     keys = torch.from_numpy(keys_np.view(np.int32)).cuda()
     out = torch.empty(n, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    heap = GHeap(capacity=n, k=k)
+    bottom_up = not args.top_down
+    heap = GHeap(capacity=n, k=k, bottom_up=bottom_up)
     heap.set_launch(ctas=args.ctas, items_per_thread=args.ipt)
     stream = torch.cuda.current_stream()
 
@@ -589,7 +596,7 @@ def run_gpu(args):
     value = 2.0 * n * args.steps * ws / (ms / 1e3)
 
     # node traffic of one step, counted by the kernel (separate untimed run)
-    cheap = GHeap(capacity=n, k=k, stats=True)
+    cheap = GHeap(capacity=n, k=k, stats=True, bottom_up=bottom_up)
     cheap.set_launch(ctas=args.ctas, items_per_thread=args.ipt)
     cheap.insert(keys)
     cheap.sync()
@@ -643,7 +650,7 @@ def run_gpu(args):
         extras["mixed"] = run_mixed(torch, ipt=args.ipt)
         extras["batched"] = run_batched(torch, tune=not args.no_tune)
         extras["serve"] = run_serve(torch)
-        extras["bottom_up"] = run_bottom_up(torch, ipt=args.ipt)
+        extras["other_variant"] = run_variant(torch, not bottom_up, ipt=args.ipt)
         extras["apps"] = run_apps(torch)
     if rank == 0:
         line = {
@@ -651,13 +658,15 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
+                       "heap": "BU-INS/TD-DEL (Section 3.3.4)" if bottom_up
+                               else "TD-INS/TD-DEL (Section 3.3.1)",
                        "keys": n, "k": k, "threads_per_block": 2 * k // args.ipt,
                        "ctas": args.ctas or "one per SM",
                        "l2": "inputs and heap (256 MB each) exceed the 126 MB L2",
                        "insert_ms": ins_avg_ms, "delete_ms": del_avg_ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": measured_traffic(dom, n, k, args.ctas)
+                         "traffic": measured_traffic(dom, n, k, args.ctas, bottom_up)
                          if args.ipt == 8 else None,
                          "peak_kind": peak_kind,
                          "kernel": "heap_kernel (%s-all launch)" % dom,
@@ -691,6 +700,8 @@ def main():
     ap.add_argument("--k", type=int, default=K)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--ipt", type=int, default=8)
+    ap.add_argument("--top-down", action="store_true",
+                    help="headline on the TD-INS/TD-DEL heap (default: BU-INS/TD-DEL)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-extras", action="store_true",
                     help="only the headline single-heap workload")
