@@ -416,7 +416,9 @@ int knapsack_create(knapsack_t *out, uint32_t max_items, uint64_t max_nodes, uin
     s->batch = batch;
     s->gc_threshold = gc_threshold;
     // every heap key names a distinct node record
-    int rc = heap_create(&s->heap, max_nodes, k, 8, 0, 0);
+    // the iterations' insert launches carry no deletes: bottom-up inserts
+    // (targets reserved without the root lock)
+    int rc = heap_create(&s->heap, max_nodes, k, 8, GHEAP_FLAG_BOTTOM_UP, 0);
     if (rc != GHEAP_OK) { s->heap = nullptr; knapsack_destroy(s); return rc; }
     bool ok = cudaMalloc(&s->d_w, (size_t)max_items * 4) == cudaSuccess &&
               cudaMalloc(&s->d_v, (size_t)max_items * 4) == cudaSuccess &&

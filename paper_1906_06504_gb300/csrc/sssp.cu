@@ -335,6 +335,9 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
     s->batch = batch;
     s->front_cap = n_edges ? n_edges : 1;
     if (heap_capacity == 0) heap_capacity = n_edges + n_vertices + 1;
+    // top-down inserts: an iteration inserts about one batch, so the root
+    // is not the bottleneck here (bottom-up inserts measured 4% slower on
+    // the 1024 x 1024 grid)
     int rc = heap_create(&s->heap, heap_capacity, k, 8, 0, 0);
     if (rc != GHEAP_OK) { s->heap = nullptr; sssp_destroy(s); return rc; }
     bool ok = cudaMalloc(&s->d_batch, (size_t)batch * 8) == cudaSuccess &&
