@@ -44,12 +44,12 @@ UNIT = "keys/s"
 # once the sources differ.
 MEASURED_TRAFFIC = {
     "sources": {
-        "gheap_kernel.cuh": "6097cb7355c91a9c410498ab8002dd2bc4d9d51cc4dfb0017c1c03705c5ebfbc",
+        "gheap_kernel.cuh": "2e187cf41ba1b381bfafb636616780f42dfc05f22fd3d89cc86aceb10e8e5ede",
         "gheap.cu": "485133b6a7f12a0ca49973a8b47aee580e70430e5d651c79c4a2bc1775028dbb",
     },
-    "bottom_up": False,
-    "insert": 710087936 + 745558784,
-    "delete": 1168293888 + 1429215232,
+    "bottom_up": True,
+    "insert": 706841344 + 748746496,
+    "delete": 1167181824 + 1429614848,
 }
 
 
