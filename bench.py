@@ -220,7 +220,7 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
             "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}
 
 
-def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
+def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=True):
     """Batched heaps: 256 heaps with log-uniform sizes 2^10 to 2^22 keys; one
     launch inserts all of them, one launch deletes all, both replayed from
     captured CUDA graphs; k and the merge width autotuned."""
@@ -230,7 +230,7 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
     total = int(sizes.sum())
     keys = inputs.keys_u32(inputs.config_seed(5), total)
     if tune:
-        best, table = tuner.autotune_set(sizes, keys, scale=0.125)
+        best, table = tuner.autotune_set(sizes, keys, scale=0.125, bottom_up=bottom_up)
     else:
         best, table = {"k": 1024, "items_per_thread": 8}, []
     k, ipt = best["k"], best["items_per_thread"]
@@ -240,7 +240,7 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
     d_del = torch.from_numpy(dele.view(np.uint8).copy()).cuda()
     d_keys = torch.from_numpy(keys.view(np.int32)).cuda()
     d_out = torch.empty(total, dtype=torch.int32, device="cuda")
-    with GHeapSet([int(x) for x in sizes], k=k) as hs:
+    with GHeapSet([int(x) for x in sizes], k=k, bottom_up=bottom_up) as hs:
         hs.set_launch(items_per_thread=ipt)
         g_ins = hs.graph(d_ins, d_keys, None)
         g_del = hs.graph(d_del, None, d_out)
@@ -269,6 +269,7 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8):
         g_del.close()
     return {"workload": "256 heaps, log-uniform 2^10..2^22 keys (%d total), insert-all + "
                         "deleteMin-all, one launch each, CUDA-graph replay" % total,
+            "insert": "bottom-up" if bottom_up else "top-down",
             "value": 2.0 * total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "k": k, "items_per_thread": ipt, "autotune": table}
 

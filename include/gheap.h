@@ -220,8 +220,11 @@ typedef struct {
 
 /* Creates a set of n_heaps slots; capacities[i] (host array) is heap i's
  * capacity in keys, 0 for an empty slot (see heapset_bind).  k, key_bytes,
- * flags and log_capacity (per heap) as for heap_create.  All heaps live on
- * the current device. */
+ * flags and log_capacity (per heap) as for heap_create.  With
+ * GHEAP_FLAG_BOTTOM_UP, a set launch whose op list holds no DEL inserts
+ * bottom-up (a small kernel checks the list on the device before the
+ * launch); lists with DELs insert top-down.  All heaps live on the current
+ * device. */
 int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities, uint32_t k,
                    uint32_t key_bytes, uint32_t flags, uint64_t log_capacity);
 

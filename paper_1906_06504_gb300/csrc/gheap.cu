@@ -502,7 +502,21 @@ struct gheapset_s {
     void *d_table;             // gh::HeapView<K>[n]
     gh::Ctl *d_ctl;
     unsigned long long *d_stats;
+    uint32_t *d_no_del;        // GHEAP_FLAG_BOTTOM_UP: the launch's list holds no DEL
 };
+
+namespace {
+
+// Clears *no_del when the op list holds an op other than INS (the flag was
+// set beforehand): a launch with only inserts may insert bottom-up.
+__global__ void set_scan_no_del(const gheapset_op *ops, unsigned long long n, uint32_t *no_del)
+{
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        if ((ops[i].kind_n >> 24) != GHEAP_OP_INS) *no_del = 0;
+}
+
+}  // namespace
 
 struct gheapset_graph_s {
     cudaGraph_t graph;
@@ -532,6 +546,17 @@ int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void 
     p.n_heaps = S->n;
     p.req_base = reinterpret_cast<const unsigned long long *>(req_base);
     p.req_cursor = reinterpret_cast<unsigned long long *>(req_cursor);
+    if ((S->flags & GHEAP_FLAG_BOTTOM_UP) && n_ops) {
+        // the kernel inserts bottom-up only when no DEL shares the launch
+        if (cudaMemsetAsync(S->d_no_del, 0xFF, sizeof(uint32_t), st) != cudaSuccess)
+            return GHEAP_ERR_CUDA;
+        const uint64_t blocks = (n_ops + 255) / 256;
+        const unsigned grid = (unsigned)(blocks < (uint64_t)S->sm_count * 2 ? blocks
+                                                                         : (uint64_t)S->sm_count * 2);
+        set_scan_no_del<<<grid, 256, 0, st>>>(ops, n_ops, S->d_no_del);
+        if (cudaGetLastError() != cudaSuccess) return GHEAP_ERR_CUDA;
+        p.set_bu = S->d_no_del;
+    }
     Shape sp;
     sp.k = S->k;
     sp.ipt = S->ipt;
@@ -602,7 +627,8 @@ int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities
     bool ok = host != nullptr &&
               cudaMalloc(&S->d_table, (size_t)n_heaps * vb) == cudaSuccess &&
               cudaMalloc((void **)&S->d_ctl, sizeof(gh::Ctl)) == cudaSuccess &&
-              cudaMalloc((void **)&S->d_stats, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc((void **)&S->d_stats, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc((void **)&S->d_no_del, sizeof(uint32_t)) == cudaSuccess;
     if (ok) {
         for (uint32_t i = 0; i < n_heaps; i++) {
             if (!S->heaps[i]) continue;   // calloc left the view zero: empty slot
@@ -634,6 +660,7 @@ int heapset_destroy(gheapset_t S)
     cudaFree(S->d_table);
     cudaFree(S->d_ctl);
     cudaFree(S->d_stats);
+    cudaFree(S->d_no_del);
     free(S);
     return GHEAP_OK;
 }

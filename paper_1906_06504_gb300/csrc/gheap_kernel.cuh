@@ -174,6 +174,7 @@ struct Params {
     const unsigned long long *req_base;   // MODE_SET cursor DELs: output base
     unsigned long long *req_cursor;       //   and running count, per request
     const unsigned long long *n_dev;      // MODE_INSERT: key count in device memory
+    const uint32_t *set_bu;      // MODE_SET: nonzero = the list has no DEL, insert bottom-up
 };
 
 // Block-shared scalars that carry decisions between the control warp and the
@@ -1759,6 +1760,9 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
     const bool multi = p.mode == MODE_SET;
     const HeapView<K> &H = multi ? set_view : p.h;
+    // a heap-set launch holding only inserts inserts bottom-up (no DEL can
+    // meet a rising batch, and every heap's node count only grows)
+    const bool set_bu = multi && p.set_bu != nullptr && *p.set_bu != 0u;
     if (threadIdx.x < N_STATS) sh.cnt[threadIdx.x] = 0;
 
     if (p.n_dev) {
@@ -1849,7 +1853,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
                 if (threadIdx.x == 0) lap(sh, STAT_INS_SORT_CYC, ts);
             }
             bar_all();
-            ok = (p.bu && p.mode == MODE_INSERT)
+            ok = ((p.bu && p.mode == MODE_INSERT) || set_bu)
                      ? ins_op<K, IPT, true>(p, H, sh, base, n, listed ? op : off)
                      : ins_op<K, IPT, false>(p, H, sh, base, n, listed ? op : off);
             if (threadIdx.x == 0) {

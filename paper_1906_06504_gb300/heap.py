@@ -280,12 +280,14 @@ class GHeapSet:
     """Many independent heaps driven by one persistent launch (include/gheap.h
     heap sets).  `heaps[i]` is a non-owning GHeap view of heap i."""
 
-    def __init__(self, capacities, k=1024, key_bytes=4, log_capacity=0, stats=False):
+    def __init__(self, capacities, k=1024, key_bytes=4, log_capacity=0, stats=False,
+                 bottom_up=False):
         L = lib()
         caps = (ctypes.c_uint64 * len(capacities))(*[int(c) for c in capacities])
         h = ctypes.c_void_p()
         _check(L.heapset_create(ctypes.byref(h), len(capacities), caps, int(k), int(key_bytes),
-                                FLAG_STATS if stats else 0, int(log_capacity)), "heapset_create")
+                                (FLAG_STATS if stats else 0) | (FLAG_BOTTOM_UP if bottom_up else 0),
+                                int(log_capacity)), "heapset_create")
         self._s = h
         self.k = int(k)
         self.key_bytes = int(key_bytes)

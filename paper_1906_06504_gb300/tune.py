@@ -21,7 +21,7 @@ def ipt_candidates(k):
     return out
 
 
-def _time_pass(torch, sizes, keys_dev, k, ipt, reps=2):
+def _time_pass(torch, sizes, keys_dev, k, ipt, reps=2, bottom_up=False):
     ins = inputs.set_phase_ops(sizes, k, OP_INS)
     dele = inputs.set_phase_ops(sizes, k, OP_DEL)
     total = int(np.sum(sizes))
@@ -29,7 +29,7 @@ def _time_pass(torch, sizes, keys_dev, k, ipt, reps=2):
     d_ins = torch.from_numpy(ins.view(np.uint8).copy()).cuda()
     d_del = torch.from_numpy(dele.view(np.uint8).copy()).cuda()
     best = None
-    with GHeapSet([int(s) for s in sizes], k=k) as hs:
+    with GHeapSet([int(s) for s in sizes], k=k, bottom_up=bottom_up) as hs:
         hs.set_launch(items_per_thread=ipt)
         for r in range(reps + 1):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -46,7 +46,8 @@ def _time_pass(torch, sizes, keys_dev, k, ipt, reps=2):
     return 2.0 * total / (best / 1e3)
 
 
-def autotune_set(sizes, keys, scale=0.25, k_candidates=K_CANDIDATES, verbose=False):
+def autotune_set(sizes, keys, scale=0.25, k_candidates=K_CANDIDATES, verbose=False,
+                 bottom_up=False):
     """Returns (best, table): best = dict(k, items_per_thread, keys_per_s) for
     a copy of the workload with every heap scaled by `scale`."""
     import torch
@@ -56,7 +57,7 @@ def autotune_set(sizes, keys, scale=0.25, k_candidates=K_CANDIDATES, verbose=Fal
     table = []
     for k in k_candidates:
         for ipt in ipt_candidates(k):
-            v = _time_pass(torch, s, keys_dev, k, ipt)
+            v = _time_pass(torch, s, keys_dev, k, ipt, bottom_up=bottom_up)
             table.append({"k": k, "items_per_thread": ipt, "keys_per_s": v})
             if verbose:
                 print("tune k=%d ipt=%d %.3e keys/s" % (k, ipt, v))

@@ -34,6 +34,9 @@ def GHeapSet(*a, **kw):
     return G(*a, **kw)
 
 
+BU = [pytest.param(False, id="top-down"), pytest.param(True, id="bottom-up")]
+
+
 class SetRun:
     """Launches op lists on a set and replays each heap's record."""
 
@@ -112,13 +115,16 @@ def random_set_ops(rng, n_heaps, k, n_ops, key_bytes, prefill=0):
     return ops, keys, int(n[~ins].sum())
 
 
+@pytest.mark.parametrize("bottom_up", BU)
 @pytest.mark.parametrize("k,key_bytes", [(64, 4), (1024, 4), (256, 8)])
-def test_heapset_random_ops_replay(k, key_bytes):
+def test_heapset_random_ops_replay(k, key_bytes, bottom_up):
+    """Mixed lists: a bottom-up set must detect the DELs and insert top-down."""
     rng = np.random.default_rng(31 + k + key_bytes)
     n_heaps = 12
     caps = [int(c) for c in rng.integers(200 * k, 300 * k, n_heaps)]
     n_ops = 3000 if k <= 256 else 1200
-    with GHeapSet(caps, k=k, key_bytes=key_bytes, log_capacity=n_ops + 64) as hs:
+    with GHeapSet(caps, k=k, key_bytes=key_bytes, log_capacity=n_ops + 64,
+                  bottom_up=bottom_up) as hs:
         run = SetRun(hs)
         ops, keys, out_size = random_set_ops(rng, n_heaps, k, n_ops, key_bytes, prefill=n_heaps * 4)
         run.launch(ops, keys, out_size)
@@ -130,16 +136,22 @@ def test_heapset_random_ops_replay(k, key_bytes):
             check_properties(h)
 
 
-def test_heapset_phased_loguniform_sizes():
+@pytest.mark.parametrize("bottom_up", BU)
+def test_heapset_phased_loguniform_sizes(bottom_up):
     """Insert-all then delete-all on 48 heaps with log-uniform sizes; in each
-    heap's root order the DEL outputs concatenate to its sorted input."""
+    heap's root order the DEL outputs concatenate to its sorted input.  A
+    bottom-up set inserts bottom-up here (the insert list has no DEL)."""
     k = 256
     sizes = inputs.loguniform_sizes(inputs.config_seed(5), 48, 8, 15)
     total = int(sizes.sum())
     keys = inputs.keys_u32(inputs.config_seed(5), total)
-    with GHeapSet([int(s) for s in sizes], k=k, log_capacity=int(-(-sizes.max() // k)) * 2 + 8) as hs:
+    with GHeapSet([int(s) for s in sizes], k=k, log_capacity=int(-(-sizes.max() // k)) * 2 + 8,
+                  bottom_up=bottom_up) as hs:
         run = SetRun(hs)
         run.launch(inputs.set_phase_ops(sizes, k, OP_INS), keys, 0)
+        hs.sync()
+        for h in hs.heaps:
+            check_properties(h)
         dops = inputs.set_phase_ops(sizes, k, OP_DEL)
         out, counts = run.launch(dops, np.empty(0, np.uint32), total)
         run.replay()
@@ -155,14 +167,15 @@ def test_heapset_phased_loguniform_sizes():
             assert hs.heaps[hid].size() == 0
 
 
-def test_heapset_graph_replay_matches_direct():
+@pytest.mark.parametrize("bottom_up", BU)
+def test_heapset_graph_replay_matches_direct(bottom_up):
     """A captured launch replayed twice (with a reset between) gives the same
     per-heap contents as the direct launch."""
     k = 128
     sizes = np.array([1000, 5000, 128, 70, 20000, 3333])
     keys = inputs.keys_u32(77, int(sizes.sum()))
     ins = inputs.set_phase_ops(sizes, k, OP_INS)
-    with GHeapSet([int(s) for s in sizes], k=k) as hs:
+    with GHeapSet([int(s) for s in sizes], k=k, bottom_up=bottom_up) as hs:
         ops_dev = torch.from_numpy(ins.view(np.uint8).copy()).cuda()
         kd = to_dev(keys)
         g = hs.graph(ops_dev, kd, None)
