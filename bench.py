@@ -220,7 +220,7 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
             "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}
 
 
-def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=True):
+def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=False):
     """Batched heaps: 256 heaps with log-uniform sizes 2^10 to 2^22 keys; one
     launch inserts all of them, one launch deletes all, both replayed from
     captured CUDA graphs; k and the merge width autotuned."""
