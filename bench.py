@@ -44,12 +44,12 @@ UNIT = "keys/s"
 # once the sources differ.
 MEASURED_TRAFFIC = {
     "sources": {
-        "gheap_kernel.cuh": "2e187cf41ba1b381bfafb636616780f42dfc05f22fd3d89cc86aceb10e8e5ede",
-        "gheap.cu": "485133b6a7f12a0ca49973a8b47aee580e70430e5d651c79c4a2bc1775028dbb",
+        "gheap_kernel.cuh": "4c8d81dfb6261caf526a2f728bd3bcd9e72cbcc80596cbf8b7764b6d51a3ac61",
+        "gheap.cu": "41c1118c0916fc12bad5f841783f5cecac2c4fba5f108bd2ab1fbfaebe06fb2e",
     },
     "bottom_up": True,
-    "insert": 706841344 + 748746496,
-    "delete": 1167181824 + 1429614848,
+    "insert": 711836672 + 749816576,
+    "delete": 1166424576 + 1428489984,
 }
 
 
