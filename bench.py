@@ -130,6 +130,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist=None):
+    """The largest of every rank's x (the job ends when its slowest rank does);
+    x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(keys_per_rank_step, steps, world_size, ms):
+    """Keys per second of the whole job: every rank's keys over the max time."""
+    return float(keys_per_rank_step) * steps * world_size / (ms / 1e3)
+
+
 def cpu_oracle_sample(n_sample):
     """Insert-all then delete-all of n_sample keys through the oracle's
     binary heap; returns (keys/s, seconds)."""
@@ -590,11 +607,8 @@ def run_gpu(args):
     ms = t_start.elapsed_time(t_end)
     ins_ms = [e[0].elapsed_time(e[1]) for e in evs]
     del_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = 2.0 * n * args.steps * ws / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_rate(2 * n, args.steps, ws, ms)
 
     # node traffic of one step, counted by the kernel (separate untimed run)
     cheap = GHeap(capacity=n, k=k, stats=True, bottom_up=bottom_up)
@@ -635,7 +649,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     assert np.array_equal(host_out.numpy().view(np.uint32)[:1024], np.sort(keys_np)[:1024])
-    e2e_value = 2.0 * n * e2e_steps * ws / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, dist)
+    e2e_value = whole_job_rate(2 * n, e2e_steps, ws, e2e_ms)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
