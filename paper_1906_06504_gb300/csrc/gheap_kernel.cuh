@@ -1,18 +1,21 @@
 // gheap_kernel.cuh -- device side of the GB300 generalized concurrent heap.
 //
-// The TD-INS/TD-DEL heap of arXiv 1906.06504 (Chen et al.):
+// The TD-INS/TD-DEL and BU-INS/TD-DEL heaps of arXiv 1906.06504 (Chen et al.):
 //   * a heap of nodes that each hold k ascending keys (Section 3.1,
 //     Properties 1-3), stored as one flat array, plus a partial buffer of at
 //     most k-1 keys guarded by the root lock (Section 3.3.2);
-//   * INS walks from the root to a target node, doing a MergeAndSort with
-//     every node on the path and carrying the k largest keys down
-//     (Section 3.2.2, top-down INS);
+//   * top-down INS walks from the root to a target node, doing a
+//     MergeAndSort with every node on the path and carrying the k largest
+//     keys down (Section 3.2.2); bottom-up INS stores its batch at the target
+//     and rises, merging with each parent until the parent is no larger
+//     (Sections 3.2.2, 3.3.4; insert-only launches);
 //   * DEL returns the root batch, refills the root from the last node and
 //     sifts down with two MergeAndSorts per level (Section 3.2.1);
 //   * every node has a multi-state lock word (AVAIL / INUSE / TARGET /
-//     MARKED, Section 3.3.2) taken with atomicCAS in parent-before-child
-//     order (Section 3.3.1), and a DEL whose last node is an in-flight INS
-//     target marks it and receives that INS's keys (Section 3.3.2);
+//     MARKED / DELIVERED, and INSHOLD for a rising batch; Sections 3.3.2,
+//     3.3.4) taken with atomicCAS in parent-before-child order (Section
+//     3.3.1), and a DEL whose last node is an in-flight INS target marks it
+//     and receives that INS's keys (Section 3.3.2);
 //   * one thread block runs one operation (Section 4); merges are block-wide
 //     (Section 4.2), batch sorting is a block bitonic sort (Section 4.1), and
 //     node pairs whose key ranges do not overlap are kept or swapped without
@@ -22,15 +25,17 @@
 // (Section 3.3.3) and each level of a walk waits on its predecessor's
 // release, so the kernel is built to shorten lock holds:
 //   * a block is nmt() "merge threads" plus one control warp.  The control
-//     warp takes every lock (an acquire stalls only that warp), issues the
+//     warp takes every lock (an acquire stalls only that warp) and issues the
 //     cp.async copies of the nodes it has locked -- for the next level while
-//     the merge threads still work on this one -- and publishes releases
-//     while the merge threads go on.  Merge threads synchronise among
-//     themselves on named barrier 1; the whole block meets on barrier 0 only
-//     where data or lock results change hands;
-//   * the root lock, the node count m and the buffer size s share one 64-bit
-//     word: acquiring the root returns the header, releasing it publishes
-//     the new one; the root is released before any deeper prefetch;
+//     the merge threads still work on this one.  Merge threads synchronise
+//     among themselves on named barrier 1; the whole block meets on barrier 0
+//     only where data or lock results change hands.  A DEL's node is
+//     released by merge thread 0 as soon as its keys are stored;
+//   * the root lock is a FIFO ticket lock whose turn shares one 64-bit word
+//     with the node count m and the buffer size s: the block whose ticket
+//     comes up reads (m, s) with the same acquire-load, and one store
+//     releases; full bottom-up batches reserve their target with an atomic
+//     add on m, without the lock;
 //   * MergeAndSort of two full nodes is a bitonic merge (shared-memory stages
 //     for wide strides, warp shuffles and registers for the rest);
 //   * persistent thread blocks pull operations from a device counter;
