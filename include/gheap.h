@@ -2,10 +2,12 @@
  * gheap.h -- C ABI of the GB300 generalized concurrent heap.
  *
  * Implements the TD-INS/TD-DEL concurrent heap of "Accelerating Concurrent
- * Heap on GPUs" (Chen, Hua, Huang, Bierema, Zhang, Zhang; arXiv 1906.06504):
+ * Heap on GPUs" (Chen, Hua, Huang, Bierema, Zhang, Zhang; arXiv 1906.06504),
+ * and its BU-INS/TD-DEL variant (GHEAP_FLAG_BOTTOM_UP, Section 3.3.4):
  * a min-heap whose nodes each hold k sorted keys (Section 3.1), insert and
  * deleteMin as top-down walks that MergeAndSort one k-batch per level
- * (Section 3.2), per-node multi-state locks taken parent before child
+ * (Section 3.2; bottom-up inserts rise from their target instead),
+ * per-node multi-state locks taken parent before child
  * (Section 3.3.1), a partial buffer at the root for batches smaller than k
  * (Section 3.3.2) and bit-reversal target placement (Section 4.3).  Every
  * operation runs on one thread block of a persistent CUDA kernel; the whole

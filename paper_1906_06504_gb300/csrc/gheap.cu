@@ -2,7 +2,8 @@
 //
 // Host side: device memory layout, launch shapes, capacity accounting and
 // error reporting.  All heap arithmetic runs in the persistent kernel of
-// gheap_kernel.cuh (TD-INS/TD-DEL heap of arXiv 1906.06504, Sections 3-4).
+// gheap_kernel.cuh (TD-INS/TD-DEL and BU-INS/TD-DEL heaps of arXiv 1906.06504,
+// Sections 3-4).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
