@@ -215,3 +215,40 @@ def test_heapset_error_is_per_heap():
         assert hs.heaps[0].size() == 4096 and hs.heaps[2].size() == 4096
         check_properties(hs.heaps[0])
         check_properties(hs.heaps[2])
+
+
+def test_heapset_insert_only_launch_runs_bottom_up():
+    """With one block the operations run in list order, so a set launch must
+    leave exactly the node layout of a single heap given the same inserts:
+    the bottom-up layout for a bottom-up set (its list holds no DEL), the
+    top-down layout otherwise.  The input is chosen so that the two layouts
+    differ."""
+    from paper_1906_06504_gb300.heap import GHeap as SingleHeap
+    k, nb = 4, 40
+    rng = np.random.default_rng(2024)
+    keys = rng.integers(0, 1000, k * nb, dtype=np.uint32)
+    sizes = np.array([keys.size])
+
+    def single(bottom_up):
+        with SingleHeap(capacity=keys.size, k=k, bottom_up=bottom_up) as h:
+            h.set_launch(ctas=1)
+            h.insert(to_dev(keys))
+            h.sync()
+            return h.snapshot()
+
+    def in_set(bottom_up):
+        with GHeapSet([keys.size], k=k, bottom_up=bottom_up) as hs:
+            hs.set_launch(ctas=1)
+            ops = inputs.set_phase_ops(sizes, k, OP_INS)
+            hs.ops(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), to_dev(keys), None)
+            hs.sync()
+            return hs.heaps[0].snapshot()
+
+    def layout(snap):
+        m = snap[3][0]
+        return snap[0][1:m + 1].copy()
+
+    bu, td = layout(single(True)), layout(single(False))
+    assert not np.array_equal(bu, td)
+    assert np.array_equal(layout(in_set(True)), bu)
+    assert np.array_equal(layout(in_set(False)), td)
