@@ -247,6 +247,11 @@ int heapset_bind(gheapset_t s, uint32_t i, gheap_t h, void *stream);
  * heap goes back to its owner. */
 int heapset_unbind(gheapset_t s, uint32_t i, void *stream);
 
+/* The set's operation counters (created with GHEAP_FLAG_STATS), summed over
+ * every launch on the set, in the order and meaning of heap_get_stats; n <=
+ * 20 (synchronizes). */
+int heapset_get_stats(gheapset_t s, uint64_t *out, uint32_t n);
+
 /* Launch shape and wait bound, as heap_set_launch / heap_set_timeout, except
  * that ctas = 0 means two blocks per SM (operations on different heaps run
  * in parallel). */

@@ -762,6 +762,18 @@ int heapset_ops_req(gheapset_t S, const gheapset_op *d_ops, uint64_t n_ops,
                                 d_req_base, d_req_cursor, (cudaStream_t)stream);
 }
 
+int heapset_get_stats(gheapset_t S, uint64_t *out, uint32_t n)
+{
+    if (!S || !out || n > gh::N_STATS) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(S->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GHEAP_ERR_CUDA;
+    unsigned long long tmp[gh::N_STATS];
+    if (cudaMemcpy(tmp, S->d_stats, sizeof(tmp), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    for (uint32_t i = 0; i < n; i++) out[i] = tmp[i];
+    return GHEAP_OK;
+}
+
 int heapset_sync(gheapset_t S)
 {
     if (!S) return GHEAP_ERR_ARG;

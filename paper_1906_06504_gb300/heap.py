@@ -75,6 +75,7 @@ def lib():
             "heapset_set_timeout": (ctypes.c_int, [vp, u64]),
             "heapset_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, vp]),
             "heapset_sync": (ctypes.c_int, [vp]),
+            "heapset_get_stats": (ctypes.c_int, [vp, u64p, u32]),
             "heapset_reset": (ctypes.c_int, [vp, vp]),
             "heapset_bind": (ctypes.c_int, [vp, u32, vp, vp]),
             "heapset_unbind": (ctypes.c_int, [vp, u32, vp]),
@@ -308,6 +309,12 @@ class GHeapSet:
     def set_launch(self, ctas=0, items_per_thread=8):
         _check(lib().heapset_set_launch(self._s, int(ctas), int(items_per_thread)),
                "heapset_set_launch")
+
+    def stats(self):
+        """The set's counters (needs stats=True), as GHeap.stats."""
+        out = (ctypes.c_uint64 * len(STAT_NAMES))()
+        _check(lib().heapset_get_stats(self._s, out, len(STAT_NAMES)), "heapset_get_stats")
+        return dict(zip(STAT_NAMES, [int(x) for x in out]))
 
     def set_timeout(self, ns):
         _check(lib().heapset_set_timeout(self._s, int(ns)), "heapset_set_timeout")

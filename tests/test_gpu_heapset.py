@@ -218,37 +218,31 @@ def test_heapset_error_is_per_heap():
 
 
 def test_heapset_insert_only_launch_runs_bottom_up():
-    """With one block the operations run in list order, so a set launch must
-    leave exactly the node layout of a single heap given the same inserts:
-    the bottom-up layout for a bottom-up set (its list holds no DEL), the
-    top-down layout otherwise.  The input is chosen so that the two layouts
-    differ."""
-    from paper_1906_06504_gb300.heap import GHeap as SingleHeap
-    k, nb = 4, 40
-    rng = np.random.default_rng(2024)
-    keys = rng.integers(0, 1000, k * nb, dtype=np.uint32)
+    """Ascending batches, one block (list order): a bottom-up insert compares
+    with one parent and stops, a top-down insert walks its whole path, so the
+    set's level counter tells which ran.  A list that holds a DEL inserts
+    top-down even in a bottom-up set."""
+    k, nb = 64, 128
+    keys = inputs.keys_u32(inputs.config_seed(5) + 9, k * nb, "ascending")
     sizes = np.array([keys.size])
+    ins = inputs.set_phase_ops(sizes, k, OP_INS)
+    # the same inserts plus one DEL of a single key at the end
+    mixed = np.concatenate([ins, inputs.set_phase_ops(np.array([1]), k, OP_DEL)])
+    # walk depth of top-down insert j (1-based slot j >= 2): floor(log2 j) levels
+    td_levels = sum(int(np.floor(np.log2(j))) for j in range(2, nb + 1))
 
-    def single(bottom_up):
-        with SingleHeap(capacity=keys.size, k=k, bottom_up=bottom_up) as h:
-            h.set_launch(ctas=1)
-            h.insert(to_dev(keys))
-            h.sync()
-            return h.snapshot()
-
-    def in_set(bottom_up):
-        with GHeapSet([keys.size], k=k, bottom_up=bottom_up) as hs:
+    def levels(bottom_up, ops):
+        with GHeapSet([keys.size], k=k, bottom_up=bottom_up, stats=True) as hs:
             hs.set_launch(ctas=1)
-            ops = inputs.set_phase_ops(sizes, k, OP_INS)
-            hs.ops(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), to_dev(keys), None)
+            out = torch.zeros(1, dtype=torch.int32, device="cuda")
+            hs.ops(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), to_dev(keys), out)
             hs.sync()
-            return hs.heaps[0].snapshot()
+            st = hs.stats()
+            if ops.size == ins.size:
+                assert st["merges"] == 0, st      # ascending: nothing to merge
+            assert hs.heaps[0].size() == keys.size - (ops.size - ins.size)
+            return st["ins_levels"]
 
-    def layout(snap):
-        m = snap[3][0]
-        return snap[0][1:m + 1].copy()
-
-    bu, td = layout(single(True)), layout(single(False))
-    assert not np.array_equal(bu, td)
-    assert np.array_equal(layout(in_set(True)), bu)
-    assert np.array_equal(layout(in_set(False)), td)
+    assert levels(True, ins) == nb - 1
+    assert levels(False, ins) == td_levels
+    assert levels(True, mixed) == td_levels
