@@ -98,8 +98,8 @@ int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
     if (grid > resident) grid = resident;
     if (grid > n_ops) grid = n_ops;
     if (grid == 0) return GHEAP_OK;
-    e = cudaMemsetAsync(sp.d_ctl, 0, sizeof(gh::Ctl), s);
-    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    // the control block is zero here: zeroed at creation and reset, and put
+    // back to zero by the last block of every launch
     kern<<<(unsigned)grid, threads, smem, s>>>(p);
     return cuda_err(cudaGetLastError());
 }
@@ -298,6 +298,7 @@ int heap_reset(gheap_t h, void *stream)
     if (cudaSetDevice(h->device) != cudaSuccess) return GHEAP_ERR_CUDA;
     cudaError_t e = cudaMemsetAsync(h->d_state, 0, ((size_t)h->max_nodes + 1) * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_hdr, 0, sizeof(gh::Hdr), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctl, 0, sizeof(gh::Ctl), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_stats, 0, gh::N_STATS * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return GHEAP_ERR_CUDA;
     h->sticky = GHEAP_OK;
@@ -637,7 +638,8 @@ int heapset_create(gheapset_t *out, uint32_t n_heaps, const uint64_t *capacities
             else fill_view(static_cast<gh::HeapView<uint64_t> *>(host)[i], S->heaps[i]);
         }
         ok = cudaMemcpy(S->d_table, host, (size_t)n_heaps * vb, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemset(S->d_stats, 0, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess;
+             cudaMemset(S->d_stats, 0, gh::N_STATS * sizeof(unsigned long long)) == cudaSuccess &&
+             cudaMemset(S->d_ctl, 0, sizeof(gh::Ctl)) == cudaSuccess;
     }
     free(host);
     if (!ok) {
@@ -796,6 +798,8 @@ int heapset_reset(gheapset_t S, void *stream)
         int rc = heap_reset(S->heaps[i], stream);
         if (rc != GHEAP_OK) return rc;
     }
+    if (cudaMemsetAsync(S->d_ctl, 0, sizeof(gh::Ctl), (cudaStream_t)stream) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
     return cuda_err(cudaMemsetAsync(S->d_stats, 0, gh::N_STATS * sizeof(unsigned long long),
                                     (cudaStream_t)stream));
 }

@@ -135,12 +135,14 @@ struct __align__(128) Hdr {
     uint32_t _p3[30];
 };
 
-// Per-launch work distribution, zeroed before every launch.
+// Per-launch work distribution.  Zero when a launch starts: zeroed when the
+// heap is created or reset, and put back to zero by the last block to leave
+// each launch (so no memset precedes a launch).
 struct __align__(16) Ctl {
     unsigned long long next_op;
     unsigned long long delivered;   // MODE_DELETE: keys handed out (root-guarded)
     uint32_t drained;               // MODE_DELETE: heap ran empty
-    uint32_t _pad;
+    uint32_t exited;                // blocks of this launch that have finished
 };
 
 // The device arrays of one heap.
@@ -1879,6 +1881,18 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     bar_all();
     if (p.stats && threadIdx.x < N_STATS && sh.cnt[threadIdx.x])
         atomicAdd(p.stats + threadIdx.x, sh.cnt[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        // every block reads the control block only before it counts itself
+        // out; the last one leaves it zero for the next launch
+        __threadfence();
+        if (atomicAdd(&p.ctl->exited, 1u) == gridDim.x - 1) {
+            p.ctl->next_op = 0;
+            p.ctl->delivered = 0;
+            p.ctl->drained = 0;
+            p.ctl->exited = 0;
+            __threadfence();
+        }
+    }
 }
 
 }  // namespace gh
