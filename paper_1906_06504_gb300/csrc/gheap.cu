@@ -381,10 +381,7 @@ int heap_delete_min(gheap_t h, void *d_out, uint64_t n, uint64_t *d_count, void 
         return GHEAP_OK;
     }
     if (!d_out) return GHEAP_ERR_ARG;
-    if (d_count) {
-        cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), (cudaStream_t)stream);
-        if (e != cudaSuccess) return GHEAP_ERR_CUDA;
-    }
+    // *d_count is written by the launch's last block
     return launch(h, gh::MODE_DELETE, nullptr, d_out, n, nullptr, 0, nullptr, d_count,
                   (cudaStream_t)stream);
 }

@@ -1886,6 +1886,9 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
         // out; the last one leaves it zero for the next launch
         __threadfence();
         if (atomicAdd(&p.ctl->exited, 1u) == gridDim.x - 1) {
+            // MODE_DELETE: the call's count is the launch's running total
+            // (also when an error stopped every operation)
+            if (p.mode == MODE_DELETE && p.out_total) *p.out_total = p.ctl->delivered;
             p.ctl->next_op = 0;
             p.ctl->delivered = 0;
             p.ctl->drained = 0;
