@@ -192,8 +192,37 @@ __global__ void __launch_bounds__(RT) sssp_relax(Graph g, const unsigned long lo
     add_stats(c, visited, edges, ins);
 }
 
+// The iteration's bookkeeping (one thread, after every append of the
+// iteration): the live-key count, the status, the next insert buffer, and the
+// report to the host.
+__device__ void finish_iteration(Ctr *c, uint32_t par, unsigned long long cap,
+                                 unsigned long long *ring, uint32_t slot)
+{
+    __threadfence();
+    volatile Ctr *vc = c;
+    const unsigned long long np = vc->popped, live0 = vc->live;
+    unsigned long long nf = vc->front[par], stalled = vc->stalled;
+    if (nf > cap && !stalled) stalled = 2;
+    if (nf > cap) nf = cap;
+    if (np > live0 && !stalled) stalled = 3;
+    if (np == 0 && live0 > 0 && !stalled) stalled = 1;
+    const unsigned long long live = np > live0 ? nf : live0 - np + nf;
+    vc->live = live;
+    vc->stalled = stalled;
+    vc->deleted = vc->deleted + np;
+    if (np) vc->iters = vc->iters + 1;
+    vc->front[par ^ 1u] = 0;          // the next iteration's insert buffer
+    vc->n_heavy = 0;
+    vc->done = 0;
+    volatile unsigned long long *r = ring;
+    r[2 * slot] = live;
+    r[2 * slot + 1] = stalled;
+    __threadfence_system();
+}
+
 // Step 3 for the queued high-degree vertices, then the iteration's
-// bookkeeping in the last block to finish.
+// bookkeeping in the last block to finish (or at once in block 0 when no
+// vertex was queued: nothing is appended then).
 __global__ void __launch_bounds__(RT) sssp_relax_heavy(Graph g, Ctr *c, uint32_t par,
                                                        unsigned long long *front,
                                                        unsigned long long cap,
@@ -202,6 +231,10 @@ __global__ void __launch_bounds__(RT) sssp_relax_heavy(Graph g, Ctr *c, uint32_t
 {
     __shared__ bool last;
     const unsigned long long nh = c->n_heavy;
+    if (nh == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) finish_iteration(c, par, cap, ring, slot);
+        return;
+    }
     unsigned long long *n_front = &c->front[par];
     unsigned long long edges = 0, ins = 0;
     for (unsigned long long h = 0; h < nh; h++) {
@@ -233,27 +266,7 @@ __global__ void __launch_bounds__(RT) sssp_relax_heavy(Graph g, Ctr *c, uint32_t
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&c->done, 1ull) == gridDim.x - 1;
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
-    __threadfence();
-    volatile Ctr *vc = c;
-    const unsigned long long np = vc->popped, live0 = vc->live;
-    unsigned long long nf = vc->front[par], stalled = vc->stalled;
-    if (nf > cap && !stalled) stalled = 2;
-    if (nf > cap) nf = cap;
-    if (np > live0 && !stalled) stalled = 3;
-    if (np == 0 && live0 > 0 && !stalled) stalled = 1;
-    const unsigned long long live = np > live0 ? nf : live0 - np + nf;
-    vc->live = live;
-    vc->stalled = stalled;
-    vc->deleted = vc->deleted + np;
-    if (np) vc->iters = vc->iters + 1;
-    vc->front[par ^ 1u] = 0;          // the next iteration's insert buffer
-    vc->n_heavy = 0;
-    vc->done = 0;
-    volatile unsigned long long *r = ring;
-    r[2 * slot] = live;
-    r[2 * slot + 1] = stalled;
-    __threadfence_system();
+    if (last && threadIdx.x == 0) finish_iteration(c, par, cap, ring, slot);
 }
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? GHEAP_OK : GHEAP_ERR_CUDA; }
