@@ -654,6 +654,76 @@ __device__ __forceinline__ void ld_run(const K *p, K (&v)[N])
     }
 }
 
+// Block bitonic sort of a[0..k) (Section 4.1) with every merge thread
+// holding E consecutive keys in registers: strides below E are exchanged in
+// registers, strides below 32·E between lanes with warp shuffles, and only
+// the wider ones pass through shared memory (6 of the 55 stages at k = 1024,
+// E = 4).  nmt()·E is a power of two >= k; when it exceeds k (one warp, small
+// k) the missing keys count as the key maximum and are never written back.
+template <typename K, int E>
+__device__ __noinline__ void block_sort_reg(K *a, uint32_t k)
+{
+    const uint32_t T = nmt(), tid = threadIdx.x;
+    const uint32_t n = T * E;
+    const uint32_t base = tid * E;
+    K v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = base + q < k ? a[base + q] : kmax<K>();
+    for (uint32_t size = 2; size <= n; size <<= 1) {
+        for (uint32_t s = size >> 1; s > 0; s >>= 1) {
+            if (s >= 32u * E) {
+                // shared-memory stage (n == k here: T > 32)
+#pragma unroll
+                for (int q = 0; q < E; ++q) a[base + q] = v[q];
+                bar_mg();
+                for (uint32_t pr = tid; pr < (n >> 1); pr += T) {
+                    const uint32_t lo = 2 * pr - (pr & (s - 1)), hi = lo + s;
+                    const bool asc = (lo & size) == 0;
+                    const K x = a[lo], y = a[hi];
+                    if ((x > y) == asc) {
+                        a[lo] = y;
+                        a[hi] = x;
+                    }
+                }
+                bar_mg();
+#pragma unroll
+                for (int q = 0; q < E; ++q) v[q] = a[base + q];
+            } else if (s >= (uint32_t)E) {
+                // partner in lane (lane ^ s/E), same register
+                const uint32_t ls = s / E;
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const uint32_t i = base + q;
+                    const K o = __shfl_xor_sync(0xffffffffu, v[q], ls);
+                    const bool keep_min = ((i & s) == 0) == ((i & size) == 0);
+                    v[q] = keep_min ? (o < v[q] ? o : v[q]) : (o < v[q] ? v[q] : o);
+                }
+            } else {
+#pragma unroll
+                for (int st = E / 2; st >= 1; st >>= 1) {
+                    if ((uint32_t)st != s) continue;
+#pragma unroll
+                    for (int q = 0; q < E; ++q) {
+                        if ((q & st) == 0) {
+                            const bool asc = ((base + q) & size) == 0;
+                            const K x = v[q], y = v[q + st];
+                            if ((x > y) == asc) {
+                                v[q] = y;
+                                v[q + st] = x;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    bar_mg();
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+        if (base + q < k) a[base + q] = v[q];
+    bar_mg();
+}
+
 // ld_run / st_run of a run wider than 16 bytes per thread, with the 16-byte
 // chunks taken in a per-thread rotated order: thread t starts at chunk
 // (t >> (3 - log2 C)) mod C, so that the 8 threads of a quarter warp cover
@@ -1856,7 +1926,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
                     cp_async_wait();
                 }
                 bar_mg();
-                block_sort(base, k);
+                block_sort_reg<K, IPT / 2>(base, k);
                 if (threadIdx.x == 0) lap(sh, STAT_INS_SORT_CYC, ts);
             }
             bar_all();
