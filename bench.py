@@ -171,6 +171,60 @@ def cpu_oracle_sample(n_sample):
     return 2 * n_sample / dt, dt
 
 
+def host_cpu():
+    """The host CPU model and logical core count, for the CPU timings."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(),
+            "arch": platform.machine(), "logical_cores": os.cpu_count()}
+
+
+def _oracle_heaps(args):
+    """Worker: insert-all then delete-all through one oracle binary heap per
+    (offset, size) of `spans`; returns the seconds spent."""
+    keys, spans = args
+    import oracle
+    t0 = time.perf_counter()
+    for off, size in spans:
+        q = oracle.BinaryHeapPQ(int(size))
+        q.push(keys[off:off + size])
+        out = q.pop(int(size), dtype=np.uint32)
+        q.close()
+        assert out.size == size
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_heapset(sizes, keys, scale=1.0 / 16):
+    """The oracle on the heap-set workload, heaps scaled by `scale`, spread
+    over every host core (independent heaps, a spawn-started pool); returns
+    (keys/s, cores, seconds)."""
+    import multiprocessing as mp
+    s = np.maximum(1, (np.asarray(sizes, dtype=np.float64) * scale).astype(np.int64))
+    offs = np.concatenate([[0], np.cumsum(s)[:-1]])
+    cores = os.cpu_count() or 1
+    order = np.argsort(-s)                    # largest heaps first, dealt round-robin
+    parts = [[] for _ in range(cores)]
+    for j, h in enumerate(order):
+        parts[j % cores].append((int(offs[h]), int(s[h])))
+    ks = np.ascontiguousarray(keys[:int(s.sum())])
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_heaps, [(ks[:1], [(0, 1)])] * cores)      # start-up, untimed
+        t0 = time.perf_counter()
+        pool.map(_oracle_heaps, [(ks, p) for p in parts if p])
+        dt = time.perf_counter() - t0
+    return 2.0 * float(s.sum()) / dt, cores, dt
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if ws > 1:
@@ -195,6 +249,7 @@ def run_reference(args):
         "config": {"workload": "insert-all + deleteMin-all, uniform u32 keys, k=1024",
                    "keys": N_KEYS, "k": K, "sample_keys": n_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host": host_cpu(),
                          "sample": "insert-all + delete-all of 2^21 of the same uniform keys "
                                    "per step, sequential binary heap, 1 thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -292,11 +347,16 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_u
             assert np.array_equal(np.sort(out[seg]), np.sort(keys[seg]))
         g_ins.close()
         g_del.close()
+    cpu_v, cores, cpu_s = cpu_oracle_heapset(sizes, keys)
     return {"workload": "256 heaps, log-uniform 2^10..2^22 keys (%d total), insert-all + "
                         "deleteMin-all, one launch each, CUDA-graph replay" % total,
             "insert": "bottom-up" if bottom_up else "top-down",
             "value": 2.0 * total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "k": k, "items_per_thread": ipt, "autotune": table}
+            "k": k, "items_per_thread": ipt, "autotune": table,
+            "cpu_oracle": {"value": cpu_v, "unit": UNIT, "cores": cores, "seconds": cpu_s,
+                           "host": host_cpu(),
+                           "sample": "the same 256 heaps scaled to 1/16 of their sizes, one "
+                                     "oracle binary heap each, spread over every host core"}}
 
 
 def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256):
@@ -664,7 +724,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         n_sample = 1 << 22
         v, dt = cpu_oracle_sample(n_sample)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": "insert-all + delete-all of the first 2^22 keys of the same seeded "
                          "uniform stream, sequential binary heap, %.1f s" % dt}
 
