@@ -184,6 +184,11 @@ def host_cpu():
                         break
     except OSError:
         pass
+    # Arm cores report a part number (MIDR): name the ones of this class of host
+    arm_parts = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+                 "0xd49": "Arm Neoverse-N2"}
+    if model in arm_parts:
+        model = "%s (part %s)" % (arm_parts[model], model)
     import platform
     return {"model": model or platform.processor() or platform.machine(),
             "arch": platform.machine(), "logical_cores": os.cpu_count()}
