@@ -550,29 +550,6 @@ __device__ __forceinline__ void s2g(K *dst, const K *src, uint32_t n)
     }
 }
 
-// Block bitonic sort of a[0..k) by the merge threads, k a power of two,
-// ascending (Section 4.1).
-template <typename K>
-__device__ __noinline__ void block_sort(K *a, uint32_t k)
-{
-    const uint32_t T = nmt();
-    for (uint32_t size = 2; size <= k; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < (k >> 1); i += T) {
-                uint32_t lo = 2 * i - (i & (stride - 1));
-                uint32_t hi = lo + stride;
-                bool asc = (lo & size) == 0;
-                K x = a[lo], y = a[hi];
-                if ((x > y) == asc) {
-                    a[lo] = y;
-                    a[hi] = x;
-                }
-            }
-            bar_mg();
-        }
-    }
-}
-
 // MergeAndSort of two ascending runs in shared memory (Section 3.2.1) by the
 // merge-path partition (Section 4.2), merge threads only: output position
 // q < split goes to dlo[q], the rest to dhi[q - split].  Thread t produces
