@@ -305,6 +305,11 @@ __device__ __forceinline__ void release_root_word(const HeapView<K> &H, const Sh
     // of the hand-over to the next ticket
     st_release64(&H.hdr->root, rw_make(m, s, sh.turn + 1));
 }
+__device__ __forceinline__ void fence_acq_rel()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
 template <typename K>
 __device__ __forceinline__ K kmax() { return ~K(0); }
 
@@ -344,6 +349,27 @@ __device__ __forceinline__ void lap(Shared &sh, uint32_t i, long long &t)
     const long long now = clock64();
     atomicAdd(&sh.cnt[i], (unsigned long long)(now - t));
     t = now;
+}
+
+// DEL: hands back the current node (the root word at the root) and `pend`, a
+// child kept locked since the level above, after a barrier that follows the
+// block's stores to both.  Two words behind one fence (fence + strong
+// stores is a release pattern for each).
+template <typename K>
+__device__ __forceinline__ void release_step(const HeapView<K> &H, Shared &sh, uint32_t *cur_w,
+                                             uint32_t *pend, uint32_t m, uint32_t s)
+{
+    if (cur_w == nullptr) {
+        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+        release_root_word(H, sh, m, s);
+        if (pend) st_release(pend, ST_AVAIL);
+    } else if (pend) {
+        fence_acq_rel();
+        st_relaxed(cur_w, ST_AVAIL);
+        st_relaxed(pend, ST_AVAIL);
+    } else {
+        st_release(cur_w, ST_AVAIL);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -874,6 +900,270 @@ __device__ __forceinline__ void merge_kk(const K *a, const K *b, K *dlo, K *dhi,
 {
     if (nmt() * IPT == 2 * k && k >= 32u * IPT) merge_full<K, IPT>(a, b, dlo, dhi, k);
     else merge_split<K, IPT>(a, k, b, k, dlo, k, dhi);
+}
+
+// Contiguous keys between shared memory and registers: the rotated form for
+// 32-byte runs, the plain one otherwise.
+template <typename K, int N>
+__device__ __forceinline__ void ld_keys(const K *p, K (&v)[N])
+{
+    if constexpr (sizeof(K) * N == 32) ld_run_rot<K, N>(p, v);
+    else ld_run<K, N>(p, v);
+}
+
+template <typename K, int N>
+__device__ __forceinline__ void st_keys(K *p, const K (&v)[N])
+{
+    if constexpr (sizeof(K) * N == 32) st_run_rot<K, N>(p, v);
+    else st_run<K, N>(p, v);
+}
+
+// First stage of MergeAndSort of two ascending k-runs (Section 3.2.1) in
+// bitonic form: lo[i] = min(a[i], b[k-1-i]) are the k smallest keys and
+// hi[i] the k largest, each a bitonic run still to be sorted.  Every merge
+// thread takes E pairs: needs nmt()*E == k.  The destinations may alias the
+// sources.  Ends with bar_mg.
+template <typename K, int E>
+__device__ __forceinline__ void bitonic_split(const K *a, const K *b, K *lo, K *hi, uint32_t k)
+{
+    const uint32_t i0 = threadIdx.x * E;
+    K x[E], yr[E], l[E], h[E];
+    ld_keys<K, E>(a + i0, x);
+    ld_keys<K, E>(b + (k - i0 - E), yr);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const K y = yr[E - 1 - e];
+        l[e] = x[e] < y ? x[e] : y;
+        h[e] = x[e] < y ? y : x[e];
+    }
+    bar_mg();
+    st_keys<K, E>(lo + i0, l);
+    st_keys<K, E>(hi + i0, h);
+    bar_mg();
+}
+
+// Sorts the bitonic run d[0..k) ascending with all merge threads, each
+// holding E consecutive keys: half-cleaner strides of 32*E keys and more in
+// shared memory (E/2 pairs per thread), smaller ones between lanes (warp
+// shuffles) and within registers.  Needs nmt()*E == k, E >= 2 and k >= 64*E.
+// Ends with bar_mg.
+template <typename K, int E>
+__device__ __noinline__ void sort_bitonic(K *d, uint32_t k)
+{
+    constexpr int P = E / 2;
+    const uint32_t u = threadIdx.x;
+    for (uint32_t st = k >> 1; st >= 32u * E; st >>= 1) {
+        const uint32_t j = u * P;
+        const uint32_t l = 2 * j - (j & (st - 1)), h = l + st;
+        K x[P], y[P];
+        ld_run<K, P>(d + l, x);
+        ld_run<K, P>(d + h, y);
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            const K mn = x[e] < y[e] ? x[e] : y[e];
+            const K mx = x[e] < y[e] ? y[e] : x[e];
+            x[e] = mn;
+            y[e] = mx;
+        }
+        st_run<K, P>(d + l, x);
+        st_run<K, P>(d + h, y);
+        bar_mg();
+    }
+    K v[E];
+    ld_keys<K, E>(d + u * E, v);
+    const uint32_t lane = u & 31u;
+#pragma unroll
+    for (uint32_t lm = 16; lm >= 1; lm >>= 1) {
+        const bool upper = (lane & lm) != 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const K o = __shfl_xor_sync(0xffffffffu, v[q], lm);
+            v[q] = upper ? (o < v[q] ? v[q] : o) : (o < v[q] ? o : v[q]);
+        }
+    }
+#pragma unroll
+    for (int st = E / 2; st >= 1; st >>= 1) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if ((q & st) == 0) {
+                const K x = v[q], y = v[q + st];
+                v[q] = x < y ? x : y;
+                v[q + st] = x < y ? y : x;
+            }
+        }
+    }
+    st_keys<K, E>(d + u * E, v);
+    bar_mg();
+}
+
+// ---- transposed form of the split and sort (4-byte keys, 2 or 4 per thread)
+//
+// The bitonic run of k = 2^n keys is held in two layouts.  Layout A gives a
+// thread E keys k/E apart -- register bits are key-index bits n-1..n-R
+// (R = log2 E), lane bits the next 5, warp bits the lowest wb = n-R-5 -- so
+// that the first R+5 stages run in registers and shuffles.  One pass through
+// shared memory turns it into layout B (E consecutive keys per thread: the
+// warp bits on top), where the last wb stages run the same way.  Between the
+// split and the sort the run is kept at swizzled positions (bits 5-9 folded
+// into bits 0-4), so that the split's stores, layout A's single-key accesses
+// and layout B's vector loads each spread over all 32 banks.
+
+template <typename K, int E>
+struct Transposed { static constexpr bool value = sizeof(K) == 4 && (E == 2 || E == 4); };
+
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 5) & 31u); }
+
+template <typename K, int E>
+__device__ __forceinline__ void ld_vec(const K *p, K (&v)[E])
+{
+    if constexpr (E == 4) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        v[0] = (K)u.x; v[1] = (K)u.y; v[2] = (K)u.z; v[3] = (K)u.w;
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        v[0] = (K)u.x; v[1] = (K)u.y;
+    }
+}
+
+template <typename K, int E>
+__device__ __forceinline__ void st_vec(K *p, const K (&v)[E])
+{
+    if constexpr (E == 4) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4((uint32_t)v[0], (uint32_t)v[1],
+                                                   (uint32_t)v[2], (uint32_t)v[3]);
+    } else {
+        *reinterpret_cast<uint2 *>(p) = make_uint2((uint32_t)v[0], (uint32_t)v[1]);
+    }
+}
+
+// v[q] <- v[q ^ xm], xm < E.
+template <typename K, int E>
+__device__ __forceinline__ void xperm(K (&v)[E], uint32_t xm)
+{
+    if (xm & 1u) {
+#pragma unroll
+        for (int q = 0; q < E; q += 2) {
+            const K t = v[q]; v[q] = v[q + 1]; v[q + 1] = t;
+        }
+    }
+    if constexpr (E == 4) {
+        if (xm & 2u) {
+            K t = v[0]; v[0] = v[2]; v[2] = t;
+            t = v[1]; v[1] = v[3]; v[3] = t;
+        }
+    }
+}
+
+// bitonic_split with the halves stored at swizzled positions, for
+// sort_bitonic_t.  Same contract otherwise.
+template <typename K, int E>
+__device__ __forceinline__ void bitonic_split_t(const K *a, const K *b, K *lo, K *hi, uint32_t k)
+{
+    const uint32_t i0 = threadIdx.x * E;
+    K x[E], yr[E], l[E], h[E];
+    ld_vec<K, E>(a + i0, x);
+    ld_vec<K, E>(b + (k - i0 - E), yr);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const K y = yr[E - 1 - e];
+        l[e] = x[e] < y ? x[e] : y;
+        h[e] = x[e] < y ? y : x[e];
+    }
+    const uint32_t s = (i0 >> 5) & 31u;
+    const uint32_t cb = i0 ^ (s & ~(uint32_t)(E - 1));
+    xperm<K, E>(l, s & (E - 1));
+    xperm<K, E>(h, s & (E - 1));
+    bar_mg();
+    st_vec<K, E>(lo + cb, l);
+    st_vec<K, E>(hi + cb, h);
+    bar_mg();
+}
+
+// sort_bitonic of a run left at swizzled positions by bitonic_split_t; the
+// sorted run is stored in plain order.  Needs nmt()*E == k, 32 <= nmt() <= 512.
+// Ends with bar_mg.
+template <typename K, int E>
+__device__ __noinline__ void sort_bitonic_t(K *d, uint32_t k)
+{
+    constexpr uint32_t R = E == 4 ? 2u : 1u;
+    const uint32_t n = 31u - __clz(k);
+    const uint32_t wb = n - R - 5u;
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const uint32_t a0 = (lane << wb) | w;
+    K v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = d[swz(((uint32_t)q << (n - R)) | a0)];
+    // layout A: strides k/2 .. k/E between registers, then k/(2E) .. 2^wb
+    // between lanes
+#pragma unroll
+    for (int st = E / 2; st >= 1; st >>= 1) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if ((q & st) == 0) {
+                const K x = v[q], y = v[q + st];
+                v[q] = x < y ? x : y;
+                v[q + st] = x < y ? y : x;
+            }
+        }
+    }
+#pragma unroll
+    for (uint32_t lm = 16; lm >= 1; lm >>= 1) {
+        const bool upper = (lane & lm) != 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const K o = __shfl_xor_sync(0xffffffffu, v[q], lm);
+            v[q] = upper ? (o < v[q] ? v[q] : o) : (o < v[q] ? o : v[q]);
+        }
+    }
+    // every thread rewrites the positions it read
+#pragma unroll
+    for (int q = 0; q < E; ++q) d[swz(((uint32_t)q << (n - R)) | a0)] = v[q];
+    bar_mg();
+    // layout B: strides 2^(wb-1) .. E between lanes, then within registers
+    const uint32_t b0 = (w << (R + 5u)) | (lane << R);
+    const uint32_t x = (b0 >> 5) & 31u;
+    ld_vec<K, E>(d + (b0 ^ (x & ~(uint32_t)(E - 1))), v);
+    xperm<K, E>(v, x & (E - 1));
+    for (uint32_t pos = wb; pos > R; --pos) {
+        const uint32_t lm = 1u << (pos - 1u - R);
+        const bool upper = (lane & lm) != 0;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const K o = __shfl_xor_sync(0xffffffffu, v[q], lm);
+            v[q] = upper ? (o < v[q] ? v[q] : o) : (o < v[q] ? o : v[q]);
+        }
+    }
+#pragma unroll
+    for (int st = E / 2; st >= 1; st >>= 1) {
+        if ((uint32_t)st < (1u << wb)) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                if ((q & st) == 0) {
+                    const K x0 = v[q], y = v[q + st];
+                    v[q] = x0 < y ? x0 : y;
+                    v[q + st] = x0 < y ? y : x0;
+                }
+            }
+        }
+    }
+    bar_mg();   // every layout-B load is done before the plain stores
+    st_vec<K, E>(d + b0, v);
+    bar_mg();
+}
+
+// The split and sort in the form the key type allows.
+template <typename K, int E>
+__device__ __forceinline__ void split_run(const K *a, const K *b, K *lo, K *hi, uint32_t k)
+{
+    if constexpr (Transposed<K, E>::value) bitonic_split_t<K, E>(a, b, lo, hi, k);
+    else bitonic_split<K, E>(a, b, lo, hi, k);
+}
+
+template <typename K, int E>
+__device__ __forceinline__ void sort_run(K *d, uint32_t k)
+{
+    if constexpr (Transposed<K, E>::value) sort_bitonic_t<K, E>(d, k);
+    else sort_bitonic<K, E>(d, k);
 }
 
 // Takes a ticket under the root lock and records the operation in the
@@ -1565,9 +1855,18 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     // ---- sift down (Section 3.2.1).  At the top of every level the block
     // has met: the current node's keys are in PB(ic), its children's lock
     // results in sh.lk[par] and their keys in PB(il), PB(ir).
+    //
+    // Split form (the block shape allows it): each MergeAndSort is a bitonic
+    // split followed by sorts of the two halves with all merge threads, so
+    // the current node's half is sorted, stored and released before the
+    // halves that go down are sorted.  The larger child is then released
+    // together with the next level's node: a DEL that follows needs both.
+    constexpr int E = IPT / 2;
+    const bool split_form = IPT >= 4 && nmt() * IPT == 2 * k && k >= 32u * IPT;
     uint32_t node = 1;
     K *cur_keys = root;
     uint32_t *cur_w = nullptr;   // nullptr = the root word
+    uint32_t *pend = nullptr;    // a child still held, released with cur_w
     uint32_t par = 0;
     for (;;) {
         const uint32_t lk0 = sh.lk[par][0], lk1 = sh.lk[par][1];
@@ -1604,7 +1903,12 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             K *const X = usel ? C : D;
             if (!ctrl) {
                 long long tm = clock64();
-                merge_kk<K, IPT>(Bc, X, Bc, X, k);
+                if (split_form) {
+                    split_run<K, E>(Bc, X, Bc, X, k);
+                    sort_run<K, E>(Bc, k);
+                } else {
+                    merge_kk<K, IPT>(Bc, X, Bc, X, k);
+                }
                 s2g(cur_keys, Bc, k);
                 // the node is final: release it as soon as the merge threads'
                 // stores are done, not after the next level's locks
@@ -1614,14 +1918,11 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     stat_add(sh, STAT_STORES, 1);
                     lap(sh, STAT_DEL_MERGE_CYC, tm);
                     long long tr = clock64();
-                    if (at_root) {
-                        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-                        release_root_word(H, sh, nm, ns);
-                    } else {
-                        st_release(cur_w, ST_AVAIL);
-                    }
+                    release_step(H, sh, cur_w, pend, nm, ns);
                     lap(sh, STAT_DEL_REL_CYC, tr);
                 }
+                // the half that goes down, sorted after the node went back
+                if (split_form) sort_run<K, E>(X, k);
             } else {
                 long long tw = clock64();
                 cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
@@ -1634,6 +1935,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             node = x;
             cur_keys = xk;
             cur_w = xw;
+            pend = nullptr;
             par ^= 1;
             continue;
         }
@@ -1671,6 +1973,89 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         uint32_t *sm_w = &H.state[sms];
         const bool big_changed = big_l ? l_changed : r_changed;
         const bool sm_changed = big_l ? r_changed : l_changed;
+        if (split_form) {
+            if (!ctrl) {
+                long long tm = clock64();
+                if (overlap) {
+                    split_run<K, E>(C, D, C, D, k);   // S = C, L = D
+                    sort_run<K, E>(C, k);
+                }
+                const bool h = cmax <= S[0];
+                // every carried key above the small half: the second
+                // MergeAndSort is a swap (Section 4.3)
+                const bool sw = !h && Bc[0] >= S[k - 1];
+                if (threadIdx.x == 0) {
+                    stat_add(sh, overlap ? STAT_MERGES : STAT_SKIPS, 1);
+                    sh.halt = h;
+                    sh.swap = sw;
+                }
+                if (!h) {
+                    if (sw) {
+                        s2g(cur_keys, S, k);
+                    } else {
+                        split_run<K, E>(Bc, S, Bc, S, k);
+                        sort_run<K, E>(Bc, k);
+                        s2g(cur_keys, Bc, k);
+                    }
+                    bar_mg();
+                    if (threadIdx.x == 0) {
+                        stat_add(sh, sw ? STAT_SKIPS : STAT_MERGES, 1);
+                        stat_add(sh, STAT_STORES, 1);
+                        lap(sh, STAT_DEL_MERGE_CYC, tm);
+                        long long tr = clock64();
+                        release_step(H, sh, cur_w, pend, nm, ns);
+                        lap(sh, STAT_DEL_REL_CYC, tr);
+                        tm = clock64();
+                    }
+                } else if (sm_changed) {
+                    s2g(sm_keys, S, k);
+                    if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+                }
+                // the halves that go down: the larger child's keys, then the
+                // carried keys (the small child's new contents)
+                if (overlap) sort_run<K, E>(L, k);
+                if (big_changed) {
+                    s2g(big_keys, L, k);
+                    if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
+                }
+                if (!h && !sw) sort_run<K, E>(S, k);
+                if (threadIdx.x == 0) lap(sh, STAT_DEL_MERGE_CYC, tm);
+            } else {
+                // the small child's children, locked and loaded meanwhile
+                long long tw = clock64();
+                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
+                                 sh.lk[par ^ 1]);
+                if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
+            }
+            bar_all();
+            const bool halt = sh.halt;
+            const bool swap2 = !halt && sh.swap;
+            if (halt) {
+                // the sift ends here (the current node keeps its keys): the
+                // children and whatever the control warp took go back; the
+                // current node and `pend` are released below the loop
+                if (ctrl && lane == 0) {
+                    st_release(big_w, ST_AVAIL);
+                    st_release(sm_w, ST_AVAIL);
+                    if (gl && sh.lk[par ^ 1][0] == ST_AVAIL) st_release(&H.state[gl], ST_AVAIL);
+                    if (gr && sh.lk[par ^ 1][1] == ST_AVAIL) st_release(&H.state[gr], ST_AVAIL);
+                }
+                break;
+            }
+            uint32_t sb = S_is_C ? il : ir;
+            const uint32_t lb = S_is_C ? ir : il;
+            uint32_t n1 = ic;
+            if (swap2) {
+                const uint32_t t = sb; sb = n1; n1 = t;
+            }
+            ic = sb; il = f1; ir = f2; f1 = n1; f2 = lb;
+            node = smn;
+            cur_keys = sm_keys;
+            cur_w = sm_w;
+            pend = big_w;
+            par ^= 1;
+            continue;
+        }
         uint32_t t_try = ST_EMPTY;
         if (!ctrl) {
             long long tm = clock64();
@@ -1781,14 +2166,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
     }
     bar_all();
-    if (ctrl && lane == 0) {
-        if (cur_w == nullptr) {
-            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
-            release_root_word(H, sh, nm, ns);
-        } else {
-            st_release(cur_w, ST_AVAIL);
-        }
-    }
+    if (ctrl && lane == 0) release_step(H, sh, cur_w, pend, nm, ns);
     return true;
 #undef PB
 }
