@@ -79,7 +79,8 @@ struct Shape {
 template <typename K, int IPT>
 int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
-    auto kern = gh::heap_kernel<K, IPT>;
+    auto kern = p.mode == gh::MODE_DELETE ? gh::heap_kernel<K, IPT, true>
+                                          : gh::heap_kernel<K, IPT, false>;
     const uint32_t threads = threads_for(sp.k, IPT);
     const size_t smem = 6u * (size_t)sp.k * sizeof(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

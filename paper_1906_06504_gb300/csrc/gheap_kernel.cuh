@@ -2180,7 +2180,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
 template <int IPT>
 struct MaxThreads { static constexpr int value = IPT >= 8 ? 288 : 544; };
 
-template <typename K, int IPT>
+// DEL_ONLY: the specialisation for delete-only launches (MODE_DELETE), built
+// without the insert, operation-list and heap-set paths so that the code a
+// deleteMin walks through stays small.
+template <typename K, int IPT, bool DEL_ONLY>
 __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<K> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2190,7 +2193,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     __shared__ unsigned long long set_off;
     const uint32_t k = p.k;
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
-    const bool multi = p.mode == MODE_SET;
+    const bool multi = !DEL_ONLY && p.mode == MODE_SET;
     const HeapView<K> &H = multi ? set_view : p.h;
     // a heap-set launch holding only inserts inserts bottom-up (no DEL can
     // meet a rising batch, and every heap's node count only grows)
@@ -2203,7 +2206,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
         p.n = nd < p.n ? nd : p.n;
     }
     unsigned long long n_ops;
-    if (p.mode == MODE_OPS || multi) n_ops = p.n_ops;
+    if (!DEL_ONLY && (p.mode == MODE_OPS || multi)) n_ops = p.n_ops;
     else n_ops = (p.n + k - 1) / k;
 
     for (;;) {
@@ -2243,7 +2246,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
         bool ok;
         uint32_t kind, n;
         unsigned long long off;
-        if (p.mode == MODE_INSERT) {
+        if (DEL_ONLY) {
+            kind = GHEAP_OP_DEL;
+            n = k;
+            off = 0;
+        } else if (p.mode == MODE_INSERT) {
             kind = GHEAP_OP_INS;
             off = op * k;
             n = (uint32_t)min((unsigned long long)k, p.n - off);
@@ -2266,8 +2273,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
             n = d.n;
             off = d.offset;
         }
-        const bool listed = p.mode == MODE_OPS || multi;
-        if (kind == GHEAP_OP_INS) {
+        const bool listed = !DEL_ONLY && (p.mode == MODE_OPS || multi);
+        if constexpr (DEL_ONLY) {
+            ok = del_op<K, IPT>(p, H, sh, base, n, off, op, nullptr, -1ll);
+            if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
+        } else if (kind == GHEAP_OP_INS) {
             // stage and sort the batch before taking the root (Section 4.1)
             if (!is_ctrl()) {
                 long long ts = clock64();
