@@ -1631,7 +1631,9 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
 // Control warp: lock the children (slots sl, sr; 0 = none) of a held node --
 // lane 0 the left, lane 1 the right, waiting as needed (`first0/1` are earlier
 // tries or NO_TRY) -- and copy the present ones into dl / dr.  Results go to
-// lk[0..1].  Returns with the copies complete.
+// lk[0..1].  Returns with the copies complete.  The warp waits as one (a vote
+// per poll, each poll a compare-and-swap that also takes the lock), so that it
+// is converged when it issues the copies.
 template <typename K>
 __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapView<K> &H,
                                                  Shared &sh, uint32_t sl, uint32_t sr,
@@ -1640,16 +1642,34 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
 {
     const uint32_t lane = clane();
     const uint32_t k = p.k;
+    uint32_t v = ST_EMPTY;
+    uint32_t *w = nullptr;
     if (lane < 2) {
         const uint32_t sx = lane ? sr : sl;
-        uint32_t v = ST_EMPTY;
         if (sx) {
-            uint32_t f = lane ? first1 : first0;
-            if (f == NO_TRY) f = try_lock(&H.state[sx]);
-            v = lock_node(p, H, sh, &H.state[sx], f);
+            w = &H.state[sx];
+            const uint32_t f = lane ? first1 : first0;
+            v = f == NO_TRY ? try_lock(w) : f;
         }
-        lk[lane] = v;
     }
+    bool pending = v == ST_INUSE;
+    if (__any_sync(0xffffffffu, pending)) {
+        if (pending) stat_add(sh, STAT_WAITS, 1);
+        unsigned long long t0 = 0;
+        uint32_t it = 0;
+        do {
+            if (pending) {
+                if (!keep_waiting(p, H, t0, it)) {
+                    v = ST_GAVE_UP;
+                    pending = false;
+                } else {
+                    v = try_lock(w);
+                    pending = v == ST_INUSE;
+                }
+            }
+        } while (__any_sync(0xffffffffu, pending));
+    }
+    if (lane < 2) lk[lane] = v;
     __syncwarp();
     if (lk[0] == ST_AVAIL) g2s(dl, H.keys + (size_t)sl * k, k, lane, 32u);
     if (lk[1] == ST_AVAIL) g2s(dr, H.keys + (size_t)sr * k, k, lane, 32u);
