@@ -54,7 +54,7 @@ int map_dev_err(uint32_t e)
 }
 
 // Threads per block: the merge threads (2k/ipt merge outputs each, at least
-// one warp, at most 512) plus one control warp.
+// one warp, at most 512) plus the control warp and the release warp.
 uint32_t merge_threads_for(uint32_t k, uint32_t ipt)
 {
     uint32_t t = 2 * k / ipt;
@@ -62,7 +62,7 @@ uint32_t merge_threads_for(uint32_t k, uint32_t ipt)
     return t;
 }
 
-uint32_t threads_for(uint32_t k, uint32_t ipt) { return merge_threads_for(k, ipt) + 32; }
+uint32_t threads_for(uint32_t k, uint32_t ipt) { return merge_threads_for(k, ipt) + 64; }
 
 // Merge threads allowed by the kernel's launch bound for this merge width.
 uint32_t max_merge_threads(uint32_t ipt) { return ipt >= 8 ? 256 : 512; }

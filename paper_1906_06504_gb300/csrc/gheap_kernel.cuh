@@ -184,6 +184,18 @@ struct Params {
     const uint32_t *set_bu;      // MODE_SET: nonzero = the list has no DEL, insert bottom-up
 };
 
+// A hand-off to the release warp: behind one fence, up to two lock words set
+// to AVAIL and the root word set to `root_v`.  `stop` ends the release warp.
+struct RelReq {
+    uint32_t *w0;
+    uint32_t *w1;
+    unsigned long long *root_w;
+    unsigned long long root_v;
+    unsigned long long t_root;    // root acquisition time (root hold statistic)
+    uint32_t stop;
+};
+constexpr uint32_t N_REQ = 4;     // request ring
+
 // Block-shared scalars that carry decisions between the control warp and the
 // merge threads (always across a block barrier).
 struct Shared {
@@ -200,6 +212,11 @@ struct Shared {
     int halt;                 // DEL: the sift ends after MergeAndSort(l, r)
     int swap;                 // DEL: MergeAndSort(cur, small child) is a swap
     uint32_t lk[2][2];        // lock results, double-buffered by level
+    // release ring: posted by merge thread 0, taken in order by the release
+    // warp (`rq_read`: requests taken, their slots free again)
+    RelReq rq[N_REQ];
+    uint32_t rq_posted, rq_read;
+    uint32_t stats_on;        // the launch counts statistics
     unsigned long long cnt[N_STATS];
 };
 
@@ -207,18 +224,45 @@ struct Shared {
 // block roles and barriers
 // ---------------------------------------------------------------------------
 
-// Merge threads are threadIdx.x < nmt(); the last warp is the control warp.
-__device__ __forceinline__ uint32_t nmt() { return blockDim.x - 32u; }
-__device__ __forceinline__ bool is_ctrl() { return threadIdx.x >= blockDim.x - 32u; }
-__device__ __forceinline__ uint32_t clane() { return threadIdx.x - (blockDim.x - 32u); }
+// Merge threads are threadIdx.x < nmt(); then the control warp (locks and
+// loads); the last warp is the release warp (the fences and lock releases
+// handed over by the merge threads, one lane).  The release warp takes part
+// in no barrier but the one at kernel start.
+__device__ __forceinline__ uint32_t nmt() { return blockDim.x - 64u; }
+__device__ __forceinline__ bool is_rel() { return threadIdx.x >= blockDim.x - 32u; }
+__device__ __forceinline__ bool is_ctrl() { return threadIdx.x >= blockDim.x - 64u; }
+__device__ __forceinline__ uint32_t clane() { return threadIdx.x - (blockDim.x - 64u); }
 
-// Whole block (named barrier 0).
-__device__ __forceinline__ void bar_all() { __syncthreads(); }
+// Merge threads and control warp (named barrier 0).
+__device__ __forceinline__ void bar_all()
+{
+    asm volatile("bar.sync 0, %0;" :: "r"(blockDim.x - 32u) : "memory");
+}
 
 // Merge threads only (named barrier 1).
 __device__ __forceinline__ void bar_mg()
 {
-    asm volatile("bar.sync 1, %0;" :: "r"(blockDim.x - 32u) : "memory");
+    asm volatile("bar.sync 1, %0;" :: "r"(blockDim.x - 64u) : "memory");
+}
+
+// Every thread of the block, release warp included (named barrier 2).
+__device__ __forceinline__ void bar_block()
+{
+    asm volatile("bar.sync 2, %0;" :: "r"(blockDim.x) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];"
+                 : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.cta.shared.u32 [%0], %1;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -338,17 +382,26 @@ __device__ __forceinline__ void child_slots(uint32_t node, uint32_t max_nodes, u
     }
 }
 
+// Statistics are counted only when the launch asks for them (the shared
+// 64-bit atomics cost a few hundred cycles on the paths they sit on).
 __device__ __forceinline__ void stat_add(Shared &sh, uint32_t i, unsigned long long v)
 {
-    atomicAdd(&sh.cnt[i], v);
+    if (sh.stats_on) atomicAdd(&sh.cnt[i], v);
 }
 
 // Phase timer of one observer thread: adds the cycles since `t`, restarts.
 __device__ __forceinline__ void lap(Shared &sh, uint32_t i, long long &t)
 {
+    if (!sh.stats_on) return;
     const long long now = clock64();
     atomicAdd(&sh.cnt[i], (unsigned long long)(now - t));
     t = now;
+}
+
+// Root hold statistic: time since the root was taken (sh.t_root).
+__device__ __forceinline__ void stat_root(Shared &sh)
+{
+    if (sh.stats_on) atomicAdd(&sh.cnt[STAT_ROOT_NS], gtimer() - sh.t_root);
 }
 
 // DEL: hands back the current node (the root word at the root) and `pend`, a
@@ -360,7 +413,7 @@ __device__ __forceinline__ void release_step(const HeapView<K> &H, Shared &sh, u
                                              uint32_t *pend, uint32_t m, uint32_t s)
 {
     if (cur_w == nullptr) {
-        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+        stat_root(sh);
         release_root_word(H, sh, m, s);
         if (pend) st_release(pend, ST_AVAIL);
     } else if (pend) {
@@ -370,6 +423,57 @@ __device__ __forceinline__ void release_step(const HeapView<K> &H, Shared &sh, u
     } else {
         st_release(cur_w, ST_AVAIL);
     }
+}
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// Spins until the shared counter *w reaches v (modulo 2^32), at most
+// `timeout_ns`.  False: gave up.
+__device__ __forceinline__ bool spin_until(const uint32_t *w, uint32_t v,
+                                           unsigned long long timeout_ns)
+{
+    unsigned long long t0 = 0;
+    for (uint32_t it = 1; (int)(ld_acquire_cta(w) - v) < 0; ++it) {
+        if ((it & 63u) == 0) {
+            const unsigned long long now = gtimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > timeout_ns) return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// The release warp (its lane 0; the other lanes leave).  Takes the requests
+// in order and, behind one fence per request, sets the named lock words to
+// AVAIL and the root word to its new value.  The keys those releases publish
+// were stored by the merge threads before the barrier that preceded the
+// post; the post and the take are a release / acquire pair in shared
+// memory, so the fence is cumulative over those stores.  Returns at a stop
+// request, or after a long idle time (a safety bound: the other warps' waits
+// are all bounded and their last request is a stop), setting rel_exited.
+template <typename K>
+__device__ void release_loop(const Params<K> &p, Shared &sh, uint32_t *rel_exited)
+{
+    if ((threadIdx.x & 31u) != 0) return;
+    const unsigned long long idle_max = 8ull * p.timeout_ns;
+    for (uint32_t next = 0;; ++next) {
+        if (!spin_until(&sh.rq_posted, next + 1, idle_max)) break;
+        const RelReq r = sh.rq[next % N_REQ];
+        st_release_cta(&sh.rq_read, next + 1);
+        if (r.stop) break;
+        long long tr = clock64();
+        fence_acq_rel();
+        if (r.root_w) st_relaxed64(r.root_w, r.root_v);
+        if (r.w0) st_relaxed(r.w0, ST_AVAIL);
+        if (r.w1) st_relaxed(r.w1, ST_AVAIL);
+        lap(sh, STAT_DEL_REL_CYC, tr);
+        if (r.root_w && sh.stats_on) atomicAdd(&sh.cnt[STAT_ROOT_NS], gtimer() - r.t_root);
+    }
+    st_release_cta(rel_exited, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -419,6 +523,42 @@ template <typename K>
 __device__ __forceinline__ void set_err(const HeapView<K> &H, uint32_t e)
 {
     atomicCAS(&H.hdr->err, E_NONE, e);
+}
+
+// Merge thread 0 (the only writer of rq_posted), after a barrier that follows
+// the shared-memory writes of the request's sources: queues `r` for the
+// release warp, waiting (bounded) for a free slot.  A wait that gives up has
+// set the heap's sticky error; the request is dropped.
+template <typename K>
+__device__ void post_rel(const Params<K> &p, const HeapView<K> &H, Shared &sh, const RelReq &r)
+{
+    const uint32_t idx = sh.rq_posted;
+    unsigned long long t0 = 0;
+    uint32_t it = 0;
+    while (idx - ld_acquire_cta(&sh.rq_read) >= N_REQ)
+        if (!keep_waiting(p, H, t0, it)) return;
+    sh.rq[idx % N_REQ] = r;
+    st_release_cta(&sh.rq_posted, idx + 1);
+}
+
+// DEL, merge thread 0 after the barrier that follows the merge threads'
+// stores of the node's keys (and of any larger child's keys since the last
+// post): the node (the root word at the root: m, s and the next turn) and
+// `pend` are released by the release warp.
+template <typename K>
+__device__ void post_step(const Params<K> &p, const HeapView<K> &H, Shared &sh,
+                          uint32_t *cur_w, uint32_t *pend, uint32_t m, uint32_t s)
+{
+    RelReq r = {};
+    r.w1 = pend;
+    if (cur_w == nullptr) {
+        r.root_w = &H.hdr->root;
+        r.root_v = rw_make(m, s, sh.turn + 1);
+        r.t_root = sh.t_root;
+    } else {
+        r.w0 = cur_w;
+    }
+    post_rel(p, H, sh, r);
 }
 
 // Root lock (also guards the partial buffer and the header).  Returns false
@@ -1246,7 +1386,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 sh.abort = !lock_root(p, H, sh, w);
                 lap(sh, STAT_INS_ACQ_CYC, tp);
                 if (!sh.abort) {
-                    sh.t_root = gtimer();
+                    if (sh.stats_on) sh.t_root = gtimer();
                     const uint32_t m = rw_m(w), s = rw_s(w);
                     sh.m = m;
                     sh.s = s;
@@ -1335,7 +1475,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         bar_all();
         if (ctrl && lane == 0) {
-            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            stat_root(sh);
             if (BU) {
                 if (fits) release_root_delta(H, 0, (int)n);
                 else release_root_delta(H, 1, (n < k ? (int)(n + s - k) : (int)s) - (int)s);
@@ -1448,7 +1588,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         if (sh.abort) return false;
         if (ctrl && lane == 0) {
             if (cur_w == nullptr) {
-                stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                stat_root(sh);
                 release_root_word(H, sh, tslot, s);
             } else {
                 st_release(cur_w, ST_AVAIL);
@@ -1516,7 +1656,7 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
     // it), store the batch at the target and hand the target over as INSHOLD
     bar_all();
     if (ctrl && lane == 0 && locked) {
-        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+        stat_root(sh);
         release_root_delta(H, 0, ds);
     }
     if (!ctrl) {
@@ -1541,7 +1681,7 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
                     sh.abort = !lock_root(p, H, sh, w);
                     sh.m = rw_m(w);
                     sh.s = rw_s(w);
-                    sh.t_root = gtimer();
+                    if (sh.stats_on) sh.t_root = gtimer();
                 } else {
                     unsigned long long t0 = 0;
                     uint32_t it = 0;
@@ -1608,7 +1748,7 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
             if (done) take_ticket(p, H, sh, GHEAP_OP_INS, n, ref);
             st_release(&H.state[cslot], ST_AVAIL);
             if (proot) {
-                stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                stat_root(sh);
                 release_root_delta(H, 0, 0);
             } else {
                 st_release(pw, done ? ST_AVAIL : me);
@@ -1728,7 +1868,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         lap(sh, STAT_DEL_ACQ_CYC, tp);
         if (!sh.abort) {
-            sh.t_root = gtimer();
+            if (sh.stats_on) sh.t_root = gtimer();
             const uint32_t m = rw_m(w), s = rw_s(w);
             sh.m = m;
             sh.s = s;
@@ -1774,7 +1914,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         bar_all();
         if (ctrl && lane == 0) {
-            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            stat_root(sh);
             release_root_word(H, sh, 0u, s - take);
         }
         return true;
@@ -1849,7 +1989,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     if (sh.abort) return false;
     if (root_gone) {
         if (ctrl && lane == 0) {
-            stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+            stat_root(sh);
             release_root_word(H, sh, 0u, tn);
         }
         return true;
@@ -1879,8 +2019,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     // Split form (the block shape allows it): each MergeAndSort is a bitonic
     // split followed by sorts of the two halves with all merge threads, so
     // the current node's half is sorted, stored and released before the
-    // halves that go down are sorted.  The larger child is then released
-    // together with the next level's node: a DEL that follows needs both.
+    // halves that go down are sorted.  The merge threads store the node's
+    // keys and go on; the release warp fences and releases the node.  The
+    // larger child is released together with the next level's node (a DEL
+    // that follows needs both).
     constexpr int E = IPT / 2;
     const bool split_form = IPT >= 4 && nmt() * IPT == 2 * k && k >= 32u * IPT;
     uint32_t node = 1;
@@ -1926,23 +2068,31 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 if (split_form) {
                     split_run<K, E>(Bc, X, Bc, X, k);
                     sort_run<K, E>(Bc, k);
+                    s2g(cur_keys, Bc, k);
+                    bar_mg();
+                    if (threadIdx.x == 0) {
+                        stat_add(sh, STAT_MERGES, 1);
+                        stat_add(sh, STAT_STORES, 1);
+                        lap(sh, STAT_DEL_MERGE_CYC, tm);
+                        post_step(p, H, sh, cur_w, pend, nm, ns);
+                    }
+                    // the half that goes down, sorted after the node went back
+                    sort_run<K, E>(X, k);
                 } else {
                     merge_kk<K, IPT>(Bc, X, Bc, X, k);
+                    s2g(cur_keys, Bc, k);
+                    // the node is final: release it as soon as the merge
+                    // threads' stores are done, not after the next level's locks
+                    bar_mg();
+                    if (threadIdx.x == 0) {
+                        stat_add(sh, STAT_MERGES, 1);
+                        stat_add(sh, STAT_STORES, 1);
+                        lap(sh, STAT_DEL_MERGE_CYC, tm);
+                        long long tr = clock64();
+                        release_step(H, sh, cur_w, pend, nm, ns);
+                        lap(sh, STAT_DEL_REL_CYC, tr);
+                    }
                 }
-                s2g(cur_keys, Bc, k);
-                // the node is final: release it as soon as the merge threads'
-                // stores are done, not after the next level's locks
-                bar_mg();
-                if (threadIdx.x == 0) {
-                    stat_add(sh, STAT_MERGES, 1);
-                    stat_add(sh, STAT_STORES, 1);
-                    lap(sh, STAT_DEL_MERGE_CYC, tm);
-                    long long tr = clock64();
-                    release_step(H, sh, cur_w, pend, nm, ns);
-                    lap(sh, STAT_DEL_REL_CYC, tr);
-                }
-                // the half that goes down, sorted after the node went back
-                if (split_form) sort_run<K, E>(X, k);
             } else {
                 long long tw = clock64();
                 cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
@@ -2010,22 +2160,18 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     sh.swap = sw;
                 }
                 if (!h) {
-                    if (sw) {
-                        s2g(cur_keys, S, k);
-                    } else {
+                    if (!sw) {
                         split_run<K, E>(Bc, S, Bc, S, k);
                         sort_run<K, E>(Bc, k);
-                        s2g(cur_keys, Bc, k);
                     }
+                    s2g(cur_keys, sw ? S : Bc, k);
                     bar_mg();
                     if (threadIdx.x == 0) {
                         stat_add(sh, sw ? STAT_SKIPS : STAT_MERGES, 1);
                         stat_add(sh, STAT_STORES, 1);
                         lap(sh, STAT_DEL_MERGE_CYC, tm);
-                        long long tr = clock64();
-                        release_step(H, sh, cur_w, pend, nm, ns);
-                        lap(sh, STAT_DEL_REL_CYC, tr);
-                        tm = clock64();
+                        post_step(p, H, sh, cur_w, pend, nm, ns);
+                        if (sh.stats_on) tm = clock64();
                     }
                 } else if (sm_changed) {
                     s2g(sm_keys, S, k);
@@ -2150,7 +2296,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     stat_add(sh, STAT_STORES, 1);
                     long long tr = clock64();
                     if (at_root) {
-                        stat_add(sh, STAT_ROOT_NS, gtimer() - sh.t_root);
+                        stat_root(sh);
                         release_root_word(H, sh, nm, ns);
                     } else {
                         st_release(cur_w, ST_AVAIL);
@@ -2181,6 +2327,18 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         par ^= 1;
     }
     // last node of the walk: write it and release it
+    if (split_form) {
+        if (!ctrl) {
+            s2g(cur_keys, PB(ic), k);
+            bar_mg();
+            if (threadIdx.x == 0) {
+                stat_add(sh, STAT_STORES, 1);
+                post_step(p, H, sh, cur_w, pend, nm, ns);
+            }
+        }
+        bar_all();
+        return true;
+    }
     if (!ctrl) {
         s2g(cur_keys, PB(ic), k);
         if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
@@ -2195,10 +2353,11 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
 // persistent kernel
 // ---------------------------------------------------------------------------
 
-// Block size bound per merge width: 512 merge threads + the control warp for
-// IPT <= 4, 256 + 32 for wider merges (fewer warps, more registers each).
+// Block size bound per merge width: 512 merge threads + the control and
+// release warps for IPT <= 4, 256 + 64 for wider merges (fewer warps, more
+// registers each).
 template <int IPT>
-struct MaxThreads { static constexpr int value = IPT >= 8 ? 288 : 544; };
+struct MaxThreads { static constexpr int value = IPT >= 8 ? 320 : 576; };
 
 // DEL_ONLY: the specialisation for delete-only launches (MODE_DELETE), built
 // without the insert, operation-list and heap-set paths so that the code a
@@ -2218,7 +2377,19 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     // a heap-set launch holding only inserts inserts bottom-up (no DEL can
     // meet a rising batch, and every heap's node count only grows)
     const bool set_bu = multi && p.set_bu != nullptr && *p.set_bu != 0u;
+    __shared__ uint32_t rel_exited;
     if (threadIdx.x < N_STATS) sh.cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        sh.rq_posted = 0;
+        sh.rq_read = 0;
+        sh.stats_on = p.stats != nullptr;
+        rel_exited = 0;
+    }
+    bar_block();
+    if (is_rel()) {
+        release_loop<K>(p, sh, &rel_exited);
+        return;
+    }
 
     if (p.n_dev) {
         // the key count was produced on the device (at most p.n)
@@ -2332,6 +2503,19 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
         // heaps go on (the failed heap's later ops are skipped)
         if (!ok && !multi) break;
         bar_all();
+    }
+    bar_all();
+    if (threadIdx.x == 0) {
+        // the release warp ends after every request before the stop; its
+        // statistics are in place once it has said so
+        const unsigned long long tmo = 8ull * p.timeout_ns;
+        if (spin_until(&sh.rq_read, sh.rq_posted - (N_REQ - 1), tmo)) {
+            RelReq r = {};
+            r.stop = 1;
+            sh.rq[sh.rq_posted % N_REQ] = r;
+            st_release_cta(&sh.rq_posted, sh.rq_posted + 1);
+        }
+        spin_until(&rel_exited, 1u, tmo);
     }
     bar_all();
     if (p.stats && threadIdx.x < N_STATS && sh.cnt[threadIdx.x])
