@@ -2016,13 +2016,14 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     // has met: the current node's keys are in PB(ic), its children's lock
     // results in sh.lk[par] and their keys in PB(il), PB(ir).
     //
-    // Split form (the block shape allows it): each MergeAndSort is a bitonic
-    // split followed by sorts of the two halves with all merge threads, so
-    // the current node's half is sorted, stored and released before the
-    // halves that go down are sorted.  The merge threads store the node's
-    // keys and go on; the release warp fences and releases the node.  The
-    // larger child is released together with the next level's node (a DEL
-    // that follows needs both).
+    // Split form (the block shape allows it): MergeAndSort(l, r) is the whole
+    // bitonic merge (both halves are needed before the next level's release);
+    // MergeAndSort(cur, small child), when not a swap, is a bitonic split and
+    // a sort of the node's half with all merge threads, the carried half
+    // being sorted after the node went back; likewise with one child.  The
+    // merge threads store the node's keys and go on; the release warp fences
+    // and releases the node.  The larger child is released together with the
+    // next level's node (a DEL that follows needs both).
     constexpr int E = IPT / 2;
     const bool split_form = IPT >= 4 && nmt() * IPT == 2 * k && k >= 32u * IPT;
     uint32_t node = 1;
@@ -2147,8 +2148,9 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             if (!ctrl) {
                 long long tm = clock64();
                 if (overlap) {
-                    split_run<K, E>(C, D, C, D, k);   // S = C, L = D
-                    sort_run<K, E>(C, k);
+                    // S = C, L = D: both halves sorted at once (the larger
+                    // child's keys are needed with the next level's release)
+                    merge_full<K, IPT>(C, D, C, D, k);
                 }
                 const bool h = cmax <= S[0];
                 // every carried key above the small half: the second
@@ -2179,7 +2181,6 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 }
                 // the halves that go down: the larger child's keys, then the
                 // carried keys (the small child's new contents)
-                if (overlap) sort_run<K, E>(L, k);
                 if (big_changed) {
                     s2g(big_keys, L, k);
                     if (threadIdx.x == 0) stat_add(sh, STAT_STORES, 1);
