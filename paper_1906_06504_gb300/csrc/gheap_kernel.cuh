@@ -2009,7 +2009,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         if (!ctrl && threadIdx.x == 0) stat_add(sh, STAT_LOADS, 1);
     }
-    bar_all();
+    if (need_last && tn > 0) bar_all();   // the merge above rewrote PB(ic)
     if (ctrl && lane == 0) lap(sh, STAT_DEL_ROOT_CYC, tp);
 
     // ---- sift down (Section 3.2.1).  At the top of every level the block
