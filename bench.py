@@ -749,7 +749,8 @@ def run_gpu(args):
             "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
                        "heap": "BU-INS/TD-DEL (Section 3.3.4)" if bottom_up
                                else "TD-INS/TD-DEL (Section 3.3.1)",
-                       "keys": n, "k": k, "threads_per_block": 2 * k // args.ipt,
+                       "keys": n, "k": k, "merge_threads_per_block": 2 * k // args.ipt,
+                       "threads_per_block": 2 * k // args.ipt + 64,
                        "ctas": args.ctas or "one per SM",
                        "l2": "inputs and heap (256 MB each) exceed the 126 MB L2",
                        "insert_ms": ins_avg_ms, "delete_ms": del_avg_ms},
