@@ -499,7 +499,8 @@ def _phased(torch, keys, k, ipt, ctas=0, bottom_up=False):
 
 def sweep_k_threads(torch, n=1 << 24):
     """Node capacity k x block size (Section 5.4): insert-only and delete-only
-    of n uniform keys; the block has 2k/ipt merge threads plus a control warp."""
+    of n uniform keys; the block has 2k/ipt merge threads plus the control and
+    release warps."""
     from paper_1906_06504_gb300 import inputs
     keys = torch.from_numpy(inputs.keys_u32(inputs.config_seed(2), n).view(np.int32)).cuda()
     for k in (64, 128, 256, 512, 1024, 2048):
@@ -509,7 +510,7 @@ def sweep_k_threads(torch, n=1 << 24):
                 continue
             ins, dele = _phased(torch, keys, k, ipt)
             yield {"sweep": "k_threads", "k": k, "items_per_thread": ipt,
-                   "threads": threads + 32, "keys": n, "insert_ms": ins, "delete_ms": dele,
+                   "threads": threads + 64, "keys": n, "insert_ms": ins, "delete_ms": dele,
                    "insert_keys_per_s": n / ins * 1e3, "delete_keys_per_s": n / dele * 1e3}
 
 
