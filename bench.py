@@ -44,12 +44,12 @@ UNIT = "keys/s"
 # removed) has these SHA-256 digests; reported as null once the code differs.
 MEASURED_TRAFFIC = {
     "sources": {
-        "gheap_kernel.cuh": "cf1eed8b65639c0c3e013fa5e82bbec2758f99be8e37b0899c2c798cce7b7a7b",
+        "gheap_kernel.cuh": "38606118ac907e08e17258c018a20628226b023cbbdfe90fe3d95667a517aee5",
         "gheap.cu": "dc7266be7a988944f747a042760fce6e4a20b3c4b42257e99ddcc8fce2561b37",
     },
     "bottom_up": True,
-    "insert": 708899840 + 749043968,
-    "delete": 1164970752 + 1428759808,
+    "insert": 707927040 + 748836608,
+    "delete": 1163220224 + 1426674944,
 }
 
 

@@ -320,12 +320,14 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// Releases (st.release.gpu) are issued by control lane 0 after a block
-// barrier that follows the merge threads' stores: the barrier orders those
-// stores before the release, and a release is cumulative over the writes its
-// thread has observed, so a block that acquires the word sees all of them
-// (the barrier + single release-store hand-off used between thread blocks by
-// split-K GEMM epilogues).
+// Releases (a st.release.gpu, or a fence.acq_rel.gpu and relaxed stores) are
+// issued by one thread after a block barrier that follows the merge threads'
+// stores -- control lane 0 or merge thread 0, or in deleteMin the release
+// warp after a shared-memory release / acquire hand-over from merge thread 0:
+// the barrier orders those stores before the release, and a release is
+// cumulative over the writes its thread has observed, so a block that
+// acquires the word sees all of them (the barrier + single release-store
+// hand-off used between thread blocks by split-K GEMM epilogues).
 // Release for launches in which full bottom-up batches reserve their target
 // slots without the lock (an atomic add on m): the holder adds its own
 // changes of m and s and the turn increment in one atomic, so that the
@@ -431,7 +433,9 @@ __device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned lon
 }
 
 // Spins until the shared counter *w reaches v (modulo 2^32), at most
-// `timeout_ns`.  False: gave up.
+// `timeout_ns`, with short sleeps between the polls (the release warp's first
+// request after a long idle time is a root release: a longer sleep there
+// measured 3% slower on a deleteMin-all).  False: gave up.
 __device__ __forceinline__ bool spin_until(const uint32_t *w, uint32_t v,
                                            unsigned long long timeout_ns)
 {
@@ -453,13 +457,15 @@ __device__ __forceinline__ bool spin_until(const uint32_t *w, uint32_t v,
 // were stored by the merge threads before the barrier that preceded the
 // post; the post and the take are a release / acquire pair in shared
 // memory, so the fence is cumulative over those stores.  Returns at a stop
-// request, or after a long idle time (a safety bound: the other warps' waits
-// are all bounded and their last request is a stop), setting rel_exited.
+// request, or after a long idle time (a safety bound, at least 20 s: the other
+// warps' waits are all bounded and their last request is a stop), setting
+// rel_exited.
 template <typename K>
 __device__ void release_loop(const Params<K> &p, Shared &sh, uint32_t *rel_exited)
 {
     if ((threadIdx.x & 31u) != 0) return;
-    const unsigned long long idle_max = 8ull * p.timeout_ns;
+    const unsigned long long idle_max =
+        8ull * p.timeout_ns > 20000000000ull ? 8ull * p.timeout_ns : 20000000000ull;
     for (uint32_t next = 0;; ++next) {
         if (!spin_until(&sh.rq_posted, next + 1, idle_max)) break;
         const RelReq r = sh.rq[next % N_REQ];
