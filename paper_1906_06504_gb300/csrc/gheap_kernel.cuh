@@ -24,20 +24,25 @@
 // GB300 organisation.  The root lock is the serial point of every operation
 // (Section 3.3.3) and each level of a walk waits on its predecessor's
 // release, so the kernel is built to shorten lock holds:
-//   * a block is nmt() "merge threads" plus one control warp.  The control
-//     warp takes every lock (an acquire stalls only that warp) and issues the
-//     cp.async copies of the nodes it has locked -- for the next level while
-//     the merge threads still work on this one.  Merge threads synchronise
-//     among themselves on named barrier 1; the whole block meets on barrier 0
-//     only where data or lock results change hands.  A DEL's node is
-//     released by merge thread 0 as soon as its keys are stored;
+//   * a block is nmt() "merge threads" plus a control warp and a release
+//     warp.  The control warp takes every lock (an acquire stalls only that
+//     warp; it polls as one converged warp) and issues the cp.async copies of
+//     the nodes it has locked -- for the next level while the merge threads
+//     still work on this one.  Merge threads synchronise among themselves on
+//     named barrier 1; merge threads and control warp meet on barrier 0 only
+//     where data or lock results change hands.  A DEL's node is released as
+//     soon as its keys are stored: the release warp takes the fence and the
+//     lock-word stores off the merge threads' path;
 //   * the root lock is a FIFO ticket lock whose turn shares one 64-bit word
 //     with the node count m and the buffer size s: the block whose ticket
 //     comes up reads (m, s) with the same acquire-load, and one store
 //     releases; full bottom-up batches reserve their target with an atomic
 //     add on m, without the lock;
 //   * MergeAndSort of two full nodes is a bitonic merge (shared-memory stages
-//     for wide strides, warp shuffles and registers for the rest);
+//     for wide strides, warp shuffles and registers for the rest), or a
+//     bitonic split and a sort of only the half that must be stored first;
+//   * delete-only launches run a kernel specialisation without the insert,
+//     list and heap-set paths;
 //   * persistent thread blocks pull operations from a device counter;
 //   * every wait is bounded by %globaltimer and reports a sticky error.
 #pragma once
@@ -2054,7 +2059,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         const bool at_root = cur_w == nullptr;
         // the next level's locks and loads run on the control warp during the
         // merges at every level, the root included; the current node is
-        // released by merge thread 0 as soon as its keys are stored
+        // released as soon as its keys are stored (by the release warp in the
+        // split form, else by merge thread 0)
 
         if (pl != pr) {
             // one child present (the other is absent or an INS target)
@@ -2158,6 +2164,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     // child's keys are needed with the next level's release)
                     merge_full<K, IPT>(C, D, C, D, k);
                 }
+                // (h cannot hold: the early stop above already took cmax <=
+                // min(c0, d0) = S[0]; kept so that the path stays complete)
                 const bool h = cmax <= S[0];
                 // every carried key above the small half: the second
                 // MergeAndSort is a swap (Section 4.3)
