@@ -1597,13 +1597,21 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         bar_all();
         if (sh.abort) return false;
-        if (ctrl && lane == 0) {
-            if (cur_w == nullptr) {
-                stat_root(sh);
-                release_root_word(H, sh, tslot, s);
-            } else {
-                st_release(cur_w, ST_AVAIL);
+        // the root word and the level-1 node are released at once by the
+        // control warp (the next operation waits for them); a node further
+        // down goes back through the release warp, so that the control warp
+        // takes the next node without the fence
+        if (lvl <= 1) {
+            if (ctrl && lane == 0) {
+                if (cur_w == nullptr) {
+                    stat_root(sh);
+                    release_root_word(H, sh, tslot, s);
+                } else {
+                    st_release(cur_w, ST_AVAIL);
+                }
             }
+        } else if (threadIdx.x == 0) {
+            post_step(p, H, sh, cur_w, nullptr, 0u, 0u);
         }
         if (at_target) {
             if (!ctrl) {
