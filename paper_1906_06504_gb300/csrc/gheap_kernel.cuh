@@ -2540,8 +2540,10 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<
     bar_all();
     if (threadIdx.x == 0) {
         // the release warp ends after every request before the stop; its
-        // statistics are in place once it has said so
-        const unsigned long long tmo = 8ull * p.timeout_ns;
+        // statistics are in place once it has said so (waits of at least a
+        // second: the release warp drains its ring within microseconds)
+        const unsigned long long tmo =
+            8ull * p.timeout_ns > 1000000000ull ? 8ull * p.timeout_ns : 1000000000ull;
         if (spin_until(&sh.rq_read, sh.rq_posted - (N_REQ - 1), tmo)) {
             RelReq r = {};
             r.stop = 1;
