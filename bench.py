@@ -305,16 +305,19 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
             "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}
 
 
-def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=False):
+def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=False,
+                best=None):
     """Batched heaps: 256 heaps with log-uniform sizes 2^10 to 2^22 keys; one
     launch inserts all of them, one launch deletes all, both replayed from
-    captured CUDA graphs; k and the merge width autotuned."""
+    captured CUDA graphs; k and the merge width autotuned (or `best`)."""
     from paper_1906_06504_gb300 import inputs, tune as tuner
     from paper_1906_06504_gb300.heap import GHeapSet, OP_INS, OP_DEL
     sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
     total = int(sizes.sum())
     keys = inputs.keys_u32(inputs.config_seed(5), total)
-    if tune:
+    if best is not None:
+        table = []
+    elif tune:
         best, table = tuner.autotune_set(sizes, keys, scale=0.125, bottom_up=bottom_up)
     else:
         best, table = {"k": 1024, "items_per_thread": 8}, []
@@ -608,7 +611,17 @@ def sweep_apps(torch):
         yield {"sweep": "apps", "app": name, **r}
 
 
-SWEEPS = {"apps": sweep_apps, "k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
+def sweep_heapset(torch):
+    """The heap-set workload of the default run (256 heaps, log-uniform sizes,
+    insert-all + deleteMin-all graph replays) at the configuration the
+    autotuner picks on GB300 (k = 2048, 16 merge outputs per thread), without
+    the tuning launches (for launch lists)."""
+    r = run_batched(torch, steps=3, best={"k": 2048, "items_per_thread": 16})
+    r.pop("autotune", None)
+    yield dict(sweep="heapset", **r)
+
+
+SWEEPS = {"apps": sweep_apps, "heapset": sweep_heapset, "k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
           "partial": sweep_partial, "levels": sweep_levels, "serve_rate": sweep_serve}
 
 
