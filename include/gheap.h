@@ -98,7 +98,8 @@ int heap_destroy(gheap_t h);
  * SM; a larger count is clamped to the blocks that fit on the device at
  * once), each of 2k/items_per_thread merge threads
  * (at least 32; at most 512 for items_per_thread 4, 256 for 8 and 16) plus
- * one control warp that takes the node locks; items_per_thread in {4, 8, 16}.
+ * one control warp that takes the node locks and one release warp that
+ * releases them for deleteMin; items_per_thread in {4, 8, 16}.
  * The paper's best setting is k = 1024 with 512 threads (Section 5.4), i.e.
  * items_per_thread = 4; the default is 8 (256 merge threads and more
  * registers per thread, measured faster on GB300), 16 for k = 2048. */
