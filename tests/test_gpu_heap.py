@@ -160,7 +160,7 @@ def test_ascending_input_never_merges():
 
 
 @pytest.mark.parametrize("k,key_bytes,partial", [(1024, 4, False), (1024, 4, True),
-                                                  (64, 8, True), (8, 4, True)])
+                                                  (2048, 4, True), (64, 8, True), (8, 4, True)])
 def test_concurrent_mixed_replay(k, key_bytes, partial):
     """A prefilled heap under alternating INS/DEL ops from all blocks (the
     ins-del pairs of Section 5.5); every DEL equals the oracle's replay."""

@@ -116,7 +116,7 @@ def random_set_ops(rng, n_heaps, k, n_ops, key_bytes, prefill=0):
 
 
 @pytest.mark.parametrize("bottom_up", BU)
-@pytest.mark.parametrize("k,key_bytes", [(64, 4), (1024, 4), (256, 8)])
+@pytest.mark.parametrize("k,key_bytes", [(64, 4), (1024, 4), (2048, 4), (256, 8)])
 def test_heapset_random_ops_replay(k, key_bytes, bottom_up):
     """Mixed lists: a bottom-up set must detect the DELs and insert top-down."""
     rng = np.random.default_rng(31 + k + key_bytes)
