@@ -552,10 +552,10 @@ __device__ void post_rel(const Params<K> &p, const HeapView<K> &H, Shared &sh, c
     st_release_cta(&sh.rq_posted, idx + 1);
 }
 
-// DEL, merge thread 0 after the barrier that follows the merge threads'
-// stores of the node's keys (and of any larger child's keys since the last
-// post): the node (the root word at the root: m, s and the next turn) and
-// `pend` are released by the release warp.
+// DEL and top-down INS, merge thread 0 after the barrier that follows the
+// merge threads' stores of the node's keys (and of any larger child's keys
+// since the last post): the node (the root word at the root: m, s and the
+// next turn) and `pend` are released by the release warp.
 template <typename K>
 __device__ void post_step(const Params<K> &p, const HeapView<K> &H, Shared &sh,
                           uint32_t *cur_w, uint32_t *pend, uint32_t m, uint32_t s)
