@@ -2394,9 +2394,16 @@ struct MaxThreads { static constexpr int value = IPT >= 8 ? 320 : 576; };
 
 // DEL_ONLY: the specialisation for delete-only launches (MODE_DELETE), built
 // without the insert, operation-list and heap-set paths so that the code a
-// deleteMin walks through stays small.
+// deleteMin walks through stays small.  The general kernel is built to fit
+// two blocks per SM at 8 or more merge outputs per thread (at most 96
+// registers): heap sets run two per SM, their operations being bound by the
+// latency of each walk, not by one root.
+template <int IPT, bool DEL_ONLY>
+struct MinBlocks { static constexpr int value = (DEL_ONLY || IPT < 8) ? 1 : 2; };
+
 template <typename K, int IPT, bool DEL_ONLY>
-__global__ void __launch_bounds__(MaxThreads<IPT>::value, 1) heap_kernel(Params<K> p)
+__global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ONLY>::value))
+    heap_kernel(Params<K> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Shared sh;
