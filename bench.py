@@ -155,6 +155,64 @@ def whole_job_rate(keys_per_rank_step, steps, world_size, ms):
     return float(keys_per_rank_step) * steps * world_size / (ms / 1e3)
 
 
+def _cpu_full_worker(args):
+    """Worker: insert-all then delete-all of n keys of `seed`, `reps` times,
+    through the oracle's binary heap or std::priority_queue; returns the
+    seconds of each run (inputs generated before the clock starts)."""
+    kind, n, reps, seed = args
+    import oracle
+    from paper_1906_06504_gb300 import inputs
+    keys = inputs.keys_u32(seed, n)
+    times = []
+    for _ in range(reps):
+        if kind == "oracle":
+            q = oracle.BinaryHeapPQ(n)
+            t0 = time.perf_counter()
+            q.push(keys)
+            out = q.pop(n, dtype=np.uint32)
+            dt = time.perf_counter() - t0
+            q.close()
+        else:
+            out, dt = oracle.stl_insert_delete(keys)
+        assert out.size == n and bool(np.all(out[1:] >= out[:-1]))
+        times.append(dt)
+        del out
+    return times
+
+
+class CpuBaselines:
+    """The sequential CPU heaps -- the oracle's binary heap and the paper's
+    std::priority_queue baseline (Table 1) -- timed on the full workload, best
+    of `reps` runs each.  Every run is a spawn-started worker process on its
+    own host core; they all run at once, while the GPU benchmark does (the
+    host has 16 cores; a run shares only the memory system with the others)."""
+
+    def __init__(self, n, seed, reps=3):
+        import multiprocessing as mp
+        self.n, self.reps = n, reps
+        self.pool = mp.get_context("spawn").Pool(2 * reps)
+        self.res = {kind: [self.pool.apply_async(_cpu_full_worker, ((kind, n, 1, seed),))
+                           for _ in range(reps)]
+                    for kind in ("oracle", "stl")}
+
+    def result(self, timeout=1800):
+        runs = {kind: [t for r in rs for t in r.get(timeout)] for kind, rs in self.res.items()}
+        self.pool.close()
+        self.pool.join()
+        n = self.n
+        what = ("the full workload: insert-all + deleteMin-all of the same %d uniform u32 keys "
+                "(one sequential heap, one thread), best of %d runs; each run a worker process "
+                "on its own host core, all %d runs at once, while the GPU benchmark runs"
+                % (n, self.reps, 2 * self.reps))
+        return {"value": 2.0 * n / min(runs["oracle"]), "unit": UNIT, "cores": 1,
+                "kind": "oracle", "host": host_cpu(), "sample": what, "same_config": True,
+                "runs_s": runs["oracle"], "build": "gcc -O3",
+                "stl_priority_queue": {"value": 2.0 * n / min(runs["stl"]), "unit": UNIT,
+                                       "cores": 1, "runs_s": runs["stl"], "build": "g++ -O3",
+                                       "what": "std::priority_queue<uint32_t> min-queue, the "
+                                               "sequential CPU heap of the paper's Table 1"}}
+
+
 def cpu_oracle_sample(n_sample):
     """Insert-all then delete-all of n_sample keys through the oracle's
     binary heap; returns (keys/s, seconds)."""
@@ -239,7 +297,7 @@ def run_reference(args):
             dist.barrier()
             dist.destroy_process_group()
             return
-    n_sample = 1 << 21
+    n_sample = 1 << 23
     vals = []
     for i in range(args.warmup + args.steps):
         v, dt = cpu_oracle_sample(n_sample)
@@ -251,12 +309,14 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "insert-all + deleteMin-all, uniform u32 keys, k=1024",
+        "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
                    "keys": N_KEYS, "k": K, "sample_keys": n_sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "host": host_cpu(),
-                         "sample": "insert-all + delete-all of 2^21 of the same uniform keys "
-                                   "per step, sequential binary heap, 1 thread"},
+                         "sample": "insert-all + delete-all of the first 2^23 of the same "
+                                   "uniform keys per step (the full 2^26-key workload takes "
+                                   "about half a minute per step on one core), sequential "
+                                   "binary heap (gcc -O3), 1 thread", "same_config": False},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -266,25 +326,51 @@ def run_reference(args):
         dist.destroy_process_group()
 
 
-def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, seed_off=0):
+def replay_ops_record(log, pre, stream, ops, out, counts, k):
+    """Replays a mixed run's linearization record through the CPU oracle's
+    binary heap (Section 3.3.3, Theorem 1): call 1 inserted the prefill, call
+    2 ran the op list.  Returns (DELs checked, all equal, oracle seconds)."""
+    import oracle
+    q = oracle.BinaryHeapPQ(int(pre.size) + int(stream.size))
+    checked, ok = 0, True
+    t0 = time.perf_counter()
+    try:
+        for e in log:
+            cid = int(e["call_id"])
+            n = int(e["kind_n"]) & 0xFFFFFF
+            ref = int(e["ref"])
+            if cid == 1:
+                q.push(pre[ref:ref + n])
+                continue
+            off = int(ops["offset"][ref])
+            if int(ops["kind"][ref]) == 1:
+                q.push(stream[off:off + n])
+            else:
+                want = q.pop(n, dtype=np.uint32)
+                ok = ok and n == int(counts[ref]) and bool(np.array_equal(out[off:off + n], want))
+                checked += 1
+    finally:
+        dt = time.perf_counter() - t0
+        q.close()
+    return checked, ok, dt
+
+
+def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, seed_off=0,
+              replay=True):
     """Mixed concurrent workload: prefill 2^24 keys, then 2^16 ins-del pairs
-    of k keys issued to all blocks at once (Section 5.5 ins-del pairs)."""
+    of k keys issued to all blocks at once (Section 5.5 ins-del pairs).  The
+    timed launch keeps its linearization record, which the CPU oracle then
+    replays: every DEL of the list is compared with the oracle's output."""
     from paper_1906_06504_gb300 import inputs
-    from paper_1906_06504_gb300.heap import GHeap, OP_DTYPE, OP_INS, OP_DEL
-    pre = inputs.keys_u32(inputs.config_seed(2) + 100 + seed_off, n_prefill)
-    stream_keys = inputs.keys_u32(inputs.config_seed(2) + 200 + seed_off, n_pairs * k)
-    ops = np.zeros(2 * n_pairs, dtype=OP_DTYPE)
-    ops["kind"][0::2] = OP_INS
-    ops["kind"][1::2] = OP_DEL
-    ops["n"] = k
-    ops["offset"][0::2] = np.arange(n_pairs, dtype=np.uint64) * k
-    ops["offset"][1::2] = np.arange(n_pairs, dtype=np.uint64) * k
+    from paper_1906_06504_gb300.heap import GHeap
+    pre, stream_keys, ops = inputs.mixed_pairs(n_prefill, n_pairs, k, seed_off)
     d_ops = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
     d_pre = torch.from_numpy(pre.view(np.int32)).cuda()
     d_in = torch.from_numpy(stream_keys.view(np.int32)).cuda()
     d_out = torch.empty(n_pairs * k, dtype=torch.int32, device="cuda")
     counts = torch.zeros(2 * n_pairs, dtype=torch.int32, device="cuda")
-    with GHeap(capacity=n_prefill + n_pairs * k, k=k) as h:
+    log_cap = n_prefill // k + 2 * n_pairs + 1024
+    with GHeap(capacity=n_prefill + n_pairs * k, k=k, log_capacity=log_cap) as h:
         h.set_launch(ctas=ctas, items_per_thread=ipt)
         h.insert(d_pre)
         h.sync()
@@ -296,13 +382,22 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
         torch.cuda.synchronize()
         h.sync()
         ms = e0.elapsed_time(e1)
-        # DELs may overtake INSs on a small heap and return fewer than k keys:
-        # check conservation instead of a fixed final size
         c = counts.cpu().numpy().astype(np.int64)
         assert h.size() == n_prefill + int(c[0::2].sum()) - int(c[1::2].sum())
+        log, total = h.log()
     moved = int(counts.sum().item())
-    return {"workload": "prefill 2^24, then 2^16 ins-del pairs of k=1024 keys, all blocks",
-            "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved}
+    r = {"workload": "prefill %d keys, then %d ins-del pairs of k=%d keys, all blocks"
+                     % (n_prefill, n_pairs, k),
+         "value": moved / (ms / 1e3), "unit": UNIT, "ms": ms, "keys": moved,
+         "record": "linearization record kept in the timed launch (%d entries)" % total}
+    if replay:
+        assert log.size == total
+        checked, ok, dt = replay_ops_record(log, pre, stream_keys, ops,
+                                            d_out.cpu().numpy().view(np.uint32), c, k)
+        r["exact"] = bool(ok and checked == n_pairs)
+        r["dels_checked"] = checked
+        r["cpu_oracle_replay_s"] = dt
+    return r
 
 
 def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=False,
@@ -636,12 +731,18 @@ def run_sweeps(names):
 
 
 def run_gpu(args):
+    ws, rank, local = dist_env()
+    # the CPU heaps run on other host cores meanwhile; their workers are
+    # spawned before this process makes its first CUDA call
+    cpu_jobs = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from paper_1906_06504_gb300 import inputs as _inputs
+        cpu_jobs = CpuBaselines(args.keys, _inputs.config_seed(2))
     import torch
     from paper_1906_06504_gb300 import build, inputs
     build.build()
     from paper_1906_06504_gb300.heap import GHeap
 
-    ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -735,17 +836,10 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    assert np.array_equal(host_out.numpy().view(np.uint32)[:1024], np.sort(keys_np)[:1024])
+    # the whole output of the last end-to-end step is the sorted input
+    assert np.array_equal(host_out.numpy().view(np.uint32), np.sort(keys_np))
     e2e_ms = max_over_ranks(e2e_ms, dist)
     e2e_value = whole_job_rate(2 * n, e2e_steps, ws, e2e_ms)
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        n_sample = 1 << 22
-        v, dt = cpu_oracle_sample(n_sample)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-               "sample": "insert-all + delete-all of the first 2^22 keys of the same seeded "
-                         "uniform stream, sequential binary heap, %.1f s" % dt}
 
     heap.close()
     extras = {}
@@ -755,6 +849,7 @@ def run_gpu(args):
         extras["serve"] = run_serve(torch)
         extras["other_variant"] = run_variant(torch, not bottom_up, ipt=args.ipt)
         extras["apps"] = run_apps(torch)
+    cpu = cpu_jobs.result() if cpu_jobs is not None else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

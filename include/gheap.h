@@ -109,6 +109,15 @@ int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread);
  * out sets the sticky GHEAP_ERR_TIMEOUT and the kernel returns. */
 int heap_set_timeout(gheap_t h, uint64_t ns);
 
+/* INS/DEL cooperation (Section 3.3.2): a DEL whose last node is the target of
+ * an INS still on its way down may mark that target and wait, holding the
+ * root, until the INS delivers its keys there -- the paper's protocol, n = 0.
+ * With n > 0 (default 64) the DEL first hands the root back and queues again
+ * up to n times, so that the operations behind it proceed while the INS
+ * lands; only the root order changes, never what a DEL returns for its place
+ * in that order. */
+int heap_set_yields(gheap_t h, uint32_t n);
+
 /* Inserts n keys (Section 3.2.2 top-down INS, Section 3.3.2 partial
  * buffer).  The keys are split into ceil(n/k) INS operations of consecutive
  * chunks of k (the last may be partial), run concurrently by the persistent
@@ -177,7 +186,7 @@ int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k,
  * (Section 4.3).  The map is its own inverse. */
 uint64_t heap_slot_to_node(uint64_t j);
 
-/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 20:
+/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 22:
  * out[0] node loads, out[1] node stores, out[2] merges, out[3] merges skipped
  * as disjoint (Section 4.3), out[4] INS ops, out[5] DEL ops, out[6] lock
  * waits that spun, out[7] sum of root-hold time in ns; then SM cycles seen
@@ -185,7 +194,9 @@ uint64_t heap_slot_to_node(uint64_t j);
  * before the children [9], DEL child-lock waits [10], child loads [11],
  * merges [12], stores + releases [13], DEL sift levels [14], INS root-lock
  * wait [15], INS batch sort [16], INS node-lock waits [17], INS level steps
- * [18], INS levels [19]. */
+ * [18], INS levels [19]; DELs that received the keys of an INS whose target
+ * they had marked (Section 3.3.2) [20], root hand-backs of DELs waiting for
+ * such an INS (heap_set_yields) [21]. */
 int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
 
 /* Test hook for the bounded waits: marks the root lock as held, with no
@@ -309,16 +320,24 @@ int heapset_graph_destroy(gheapset_graph_t g);
  *   - n may be at most GHEAP_NOALLOC_MAX_KEYS; larger n returns
  *     GHEAP_ERR_TOO_LARGE and enqueues nothing.  n = 0 does nothing.
  *   - The first call on each device looks up that device's address of the
- *     scratch array (a synchronous CUDA runtime query) with that device
- *     current; make that first call before any stream capture.  Later calls
- *     only enqueue work on `stream` and allocate nothing.
+ *     scratch array (a synchronous CUDA runtime query, once, even when host
+ *     threads race to make that call) with that device current; make that
+ *     first call before any stream capture.  No call allocates.
  *   - Every call shares the one scratch array: calls whose work overlaps on
  *     the GPU (different streams, or other host threads) race and corrupt
  *     each other.  Each call clears the heap state it needs, so a call never
  *     depends on what the previous call left in the array.
- *   - Device-side lock waits are bounded as for heap_insert; such a failure
- *     is not reported by this entry point (the output would then be
- *     incomplete).
+ *   - Device-side lock waits are bounded as for heap_insert.  When one runs
+ *     out (or the device sees an impossible node state) the call's output is
+ *     incomplete: the keys it did not write are set to 0xFFFFFFFF, and the
+ *     failure is kept in the scratch array.  The next call on the same stream
+ *     first waits for the stream, reads that record, and, if the previous call
+ *     failed, returns its error (GHEAP_ERR_TIMEOUT or GHEAP_ERR_STATE),
+ *     clears the record and enqueues nothing; a call after it runs normally.
+ *     Every call therefore synchronizes `stream` once before it enqueues.
+ *   - The scratch address is looked up once per device for the life of the
+ *     process; after a cudaDeviceReset the library must not be called again
+ *     on that device.
  * ------------------------------------------------------------------------ */
 #define GHEAP_NOALLOC_MAX_KEYS (1ull << 20)
 int heap_sort_noalloc(const uint32_t *d_in, uint32_t *d_out, uint64_t n, void *stream);

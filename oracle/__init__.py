@@ -15,11 +15,15 @@ Contents
 * ``check_properties`` -- Properties 1-3 of Section 3.1 on a heap snapshot.
 * ``dijkstra`` / ``knapsack_dp`` -- textbook solvers for the Section 5.7
   applications.
+* ``stl_insert_delete`` -- the paper's sequential CPU baseline (Table 1):
+  the C++ standard library's ``std::priority_queue`` (``stl_pq.cpp``), timed
+  beside the GPU heap; not part of the oracle's checks.
 * ``genheap.GeneralizedHeapModel`` -- a slow sequential model of the
   generalized heap's INS/DEL steps (Sections 3.1-3.3.2, 4.3), for node-level
   parity of a single-CTA GPU run.
 
-The C part is built with gcc on first use (or by ``build()``).
+The C and C++ parts are built with gcc/g++ -O3 on first use (or by
+``build()``).
 """
 import ctypes
 import os
@@ -31,20 +35,29 @@ import numpy as np
 _DIR = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_DIR, "heap_oracle.c")
 _SO = os.path.join(_DIR, "liboracle.so")
+_STL_SRC = os.path.join(_DIR, "stl_pq.cpp")
+_STL_SO = os.path.join(_DIR, "libstlpq.so")
 _lock = threading.Lock()
 _lib = None
+_stl = None
+
+
+def _compile(cmd, src, so, force):
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(src)):
+        return so
+    tmp = so + ".%d.tmp" % os.getpid()
+    subprocess.check_call(cmd + ["-shared", "-fPIC", "-o", tmp, src])
+    os.replace(tmp, so)
+    return so
 
 
 def build(force=False):
-    """Compile heap_oracle.c into liboracle.so next to it (plain gcc -O2)."""
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
-    os.replace(tmp, _SO)
-    return _SO
+    """Compile heap_oracle.c into liboracle.so (gcc -O3) and the standard
+    library priority-queue baseline stl_pq.cpp into libstlpq.so (g++ -O3),
+    next to them."""
+    _compile(["g++", "-O3", "-std=c++17"], _STL_SRC, _STL_SO, force)
+    return _compile(["gcc", "-O3", "-std=c11"], _SRC, _SO, force)
 
 
 def lib():
@@ -85,6 +98,28 @@ def lib():
                                           ctypes.c_uint64]
             _lib = L
     return _lib
+
+
+def stl_insert_delete(keys):
+    """The paper's sequential CPU baseline (Table 1, std::priority_queue):
+    pushes every uint32 key, then pops them all.  Returns (sorted output,
+    seconds spent in the pushes and pops)."""
+    global _stl
+    with _lock:
+        if _stl is None:
+            build()
+            L = ctypes.CDLL(_STL_SO)
+            L.stl_insert_delete_u32.restype = ctypes.c_double
+            L.stl_insert_delete_u32.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_uint32)]
+            _stl = L
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    out = np.empty_like(keys)
+    dt = _stl.stl_insert_delete_u32(_p(keys, ctypes.c_uint32), keys.size,
+                                    _p(out, ctypes.c_uint32))
+    if dt < 0:
+        raise MemoryError("std::priority_queue storage allocation failed")
+    return out, float(dt)
 
 
 def _p(arr, ctype):

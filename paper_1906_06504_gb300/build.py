@@ -1,8 +1,9 @@
 """Builds the CUDA shared library behind include/gheap.h, in-tree.
 
 nvcc -gencode arch=compute_103a,code=sm_103a (GB300) -> libgheap.so next to
-this file: gheap.cu (the heap and its C ABI) and apps.cu (applications built
-on that ABI).  Rebuilds when a source is newer than the library.
+this file: every .cu file of csrc/ -- gheap.cu (the heap and its C ABI),
+sssp.cu and knapsack.cu (the applications built on that ABI) -- compiled in
+parallel and linked once.  Rebuilds when a source is newer than the library.
 """
 import glob
 import os

@@ -9,6 +9,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "gheap.h"
 #include "gheap_kernel.cuh"
 
@@ -30,6 +33,7 @@ struct gheap_s {
     uint32_t ctas;           // 0 = one block per SM
     uint32_t ipt;            // merge outputs per thread: 2, 4 or 8
     uint64_t timeout_ns;
+    uint32_t del_yields;     // root hand-backs before a DEL marks an in-flight target
     int sm_count;
     int sticky;              // host copy of a sticky device error
     uint64_t size_upper;     // upper bound on the keys held
@@ -143,6 +147,7 @@ gh::Params<K> base_params(gheap_t h, uint32_t mode)
     p.stats = (h->flags & GHEAP_FLAG_STATS) ? h->d_stats : nullptr;
     p.k = h->k;
     p.timeout_ns = h->timeout_ns;
+    p.del_yields = h->del_yields;
     p.mode = mode;
     p.bu = (h->flags & GHEAP_FLAG_BOTTOM_UP) ? 1u : 0u;
     p.call_id = ++h->call_id;
@@ -250,6 +255,7 @@ int heap_create(gheap_t *out, uint64_t capacity_keys, uint32_t k, uint32_t key_b
     h->ctas = 0;
     h->ipt = k >= 2048 ? 16 : 8;
     h->timeout_ns = 2000000000ull;
+    h->del_yields = gh::DEL_YIELDS;
     h->log_cap = log_capacity;
 
     size_t key_bytes_total = ((size_t)h->max_nodes + 1) * k * key_bytes;
@@ -323,6 +329,13 @@ int heap_set_timeout(gheap_t h, uint64_t ns)
 {
     if (!h || ns == 0) return GHEAP_ERR_ARG;
     h->timeout_ns = ns;
+    return GHEAP_OK;
+}
+
+int heap_set_yields(gheap_t h, uint32_t n)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    h->del_yields = n;
     return GHEAP_OK;
 }
 
@@ -537,6 +550,7 @@ int set_launch(gheapset_t S, const gheapset_op *ops, uint64_t n_ops, const void 
     p.mode = gh::MODE_SET;
     p.call_id = ++S->call_id;
     p.timeout_ns = S->timeout_ns;
+    p.del_yields = gh::DEL_YIELDS;
     p.in = static_cast<const K *>(in);
     p.out = static_cast<K *>(out);
     p.n_ops = n_ops;
@@ -860,8 +874,11 @@ constexpr uint32_t NA_K = 1024;
 constexpr uint32_t NA_MAX_NODES = (uint32_t)(GHEAP_NOALLOC_MAX_KEYS / NA_K) + 1;
 constexpr size_t NA_SLOTS = (size_t)NA_MAX_NODES + 1;
 constexpr size_t na_round(size_t b) { return (b + 255) / 256 * 256; }
-constexpr size_t NA_OFF_HDR = 0;
-constexpr size_t NA_OFF_CTL = na_round(sizeof(gh::Hdr));
+// The status word of the last call comes first, outside the region each call
+// clears, so that the next call can still read it.
+constexpr size_t NA_OFF_STATUS = 0;
+constexpr size_t NA_OFF_HDR = 256;
+constexpr size_t NA_OFF_CTL = NA_OFF_HDR + na_round(sizeof(gh::Hdr));
 constexpr size_t NA_OFF_CNT = NA_OFF_CTL + na_round(sizeof(gh::Ctl));
 constexpr size_t NA_OFF_STATE = NA_OFF_CNT + 256;
 constexpr size_t NA_OFF_BUF = NA_OFF_STATE + na_round(NA_SLOTS * sizeof(uint32_t));
@@ -869,12 +886,32 @@ constexpr size_t NA_OFF_KEYS = NA_OFF_BUF + na_round(NA_K * sizeof(uint32_t));
 constexpr size_t NA_BYTES = NA_OFF_KEYS + NA_SLOTS * NA_K * sizeof(uint32_t);
 
 constexpr int NA_MAX_DEVICES = 64;
-unsigned char *na_base[NA_MAX_DEVICES];   // per-device address of the array
+// per-device address of the array, filled once under its std::call_once
+std::atomic<unsigned char *> na_base[NA_MAX_DEVICES];
+std::once_flag na_once[NA_MAX_DEVICES];
+
+// After the delete launch: when it wrote fewer than n keys (a bounded wait
+// gave up, or the device saw an impossible state), the rest of d_out gets the
+// key maximum and the status word the device error; otherwise the status
+// word is cleared.
+__global__ void na_finish(unsigned char *base, uint32_t *d_out, unsigned long long n)
+{
+    const unsigned long long got = *reinterpret_cast<const unsigned long long *>(base + NA_OFF_CNT);
+    const uint32_t err = reinterpret_cast<const gh::Hdr *>(base + NA_OFF_HDR)->err;
+    const unsigned long long from = got < n ? got : n;
+    for (unsigned long long i = from + blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+         i < n; i += (unsigned long long)gridDim.x * blockDim.x)
+        d_out[i] = 0xFFFFFFFFu;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *reinterpret_cast<uint32_t *>(base + NA_OFF_STATUS) =
+            err != gh::E_NONE ? err : (got < n ? (uint32_t)gh::E_STATE : (uint32_t)gh::E_NONE);
+}
 
 }  // namespace
 
-// Header, launch counters, a count word, node states, the partial buffer and
-// (max_nodes + 1) node batches of one k = 1024 heap, each section 256-aligned.
+// The last call's status word, then the header, launch counters, a count
+// word, node states, the partial buffer and (max_nodes + 1) node batches of
+// one k = 1024 heap, each section 256-aligned.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 extern "C" {
@@ -887,21 +924,35 @@ int heap_sort_noalloc(const uint32_t *d_in, uint32_t *d_out, uint64_t n, void *s
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GHEAP_ERR_CUDA;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return GHEAP_ERR_ARG;
-    unsigned char *base = na_base[dev];
-    if (!base) {
-        // once per device, with that device current: the host-side name of
-        // the array is not its device address
-        if (cudaGetSymbolAddress((void **)&base, g_noalloc_scratch) != cudaSuccess || !base)
-            return GHEAP_ERR_CUDA;
-        na_base[dev] = base;
-    }
+    // once per device, with that device current: the host-side name of the
+    // array is not its device address
+    std::call_once(na_once[dev], [dev] {
+        unsigned char *b = nullptr;
+        if (cudaGetSymbolAddress((void **)&b, g_noalloc_scratch) == cudaSuccess && b)
+            na_base[dev].store(b);
+    });
+    unsigned char *base = na_base[dev].load();
+    if (!base) return GHEAP_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GHEAP_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // the previous call's status (it is complete once the stream is: calls on
+    // one stream are ordered); a failure is reported now, once
+    uint32_t last = gh::E_NONE;
+    if (cudaMemcpyAsync(&last, base + NA_OFF_STATUS, sizeof(last), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
+    if (last != gh::E_NONE) {
+        if (cudaMemsetAsync(base + NA_OFF_STATUS, 0, sizeof(uint32_t), s) != cudaSuccess)
+            return GHEAP_ERR_CUDA;
+        return map_dev_err(last);
+    }
     // the root word, ticket counter, error word, launch counters and node
     // states must start at zero; keys and the partial buffer need not
-    if (cudaMemsetAsync(base, 0, NA_OFF_BUF, s) != cudaSuccess) return GHEAP_ERR_CUDA;
+    if (cudaMemsetAsync(base + NA_OFF_HDR, 0, NA_OFF_BUF - NA_OFF_HDR, s) != cudaSuccess)
+        return GHEAP_ERR_CUDA;
     gh::Params<uint32_t> p;
     memset(&p, 0, sizeof(p));
     p.h.keys = reinterpret_cast<uint32_t *>(base + NA_OFF_KEYS);
@@ -930,7 +981,10 @@ int heap_sort_noalloc(const uint32_t *d_in, uint32_t *d_out, uint64_t n, void *s
     p.in = nullptr;
     p.out = d_out;
     p.out_total = reinterpret_cast<unsigned long long *>(base + NA_OFF_CNT);
-    return launch_k<uint32_t>(sp, p, n_ops, s);
+    rc = launch_k<uint32_t>(sp, p, n_ops, s);
+    if (rc != GHEAP_OK) return rc;
+    na_finish<<<(unsigned)sms, 256, 0, s>>>(base, d_out, n);
+    return cuda_err(cudaGetLastError());
 }
 
 int heap_debug_hold_root(gheap_t h, void *stream)

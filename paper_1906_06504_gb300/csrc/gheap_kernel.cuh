@@ -71,7 +71,8 @@ __host__ __device__ __forceinline__ uint32_t inshold(uint32_t owner)
 }
 constexpr uint32_t ST_GAVE_UP = ~0u;
 // How often a DEL hands the root back rather than wait, holding it, for an
-// INS still on its way to the last node.
+// INS still on its way to the last node (the default of Params::del_yields;
+// 0 is the paper's protocol: mark the target at once and wait for delivery).
 constexpr uint32_t DEL_YIELDS = 64;
 constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
@@ -96,7 +97,9 @@ enum : uint32_t {
     STAT_INS_WAIT_CYC = 17,     // control warp: node locks and copies
     STAT_INS_STEP_CYC = 18,     // merge threads: level steps
     STAT_INS_LEVELS = 19,       // levels visited
-    N_STATS = 20
+    STAT_DELIVERIES = 20,       // DELs that received a marked target's keys (Section 3.3.2)
+    STAT_DEL_YIELDS = 21,       // DELs that handed the root back to let an INS land first
+    N_STATS = 22
 };
 
 // Root word: bits 0-29 m (full nodes), bits 30-41 s (partial-buffer keys),
@@ -173,6 +176,8 @@ struct Params {
     uint32_t call_id;
     uint32_t bu;                 // MODE_INSERT: bottom-up inserts (Section 3.3.4)
     unsigned long long timeout_ns;
+    uint32_t del_yields;         // hand-backs allowed before a DEL marks an in-flight target
+    uint32_t _pad0;
     const K *in;                 // MODE_INSERT / MODE_OPS input keys
     K *out;                      // MODE_DELETE / MODE_OPS output keys
     unsigned long long n;        // MODE_INSERT: keys; MODE_DELETE: keys wanted
@@ -653,6 +658,7 @@ __device__ bool take_last(const Params<K> &p, const HeapView<K> &H, Shared &sh, 
                     v = ld_relaxed(w);
                     if (v == ST_DELIVERED) {
                         __threadfence();
+                        stat_add(sh, STAT_DELIVERIES, 1);
                         return true;
                     }
                     if (v != ST_MARKED) {
@@ -1877,9 +1883,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 w_now = rem < want ? (uint32_t)rem : want;
             }
             const uint32_t t_now = w_now < (m >= 1 ? k : s) ? w_now : (m >= 1 ? k : s);
-            if (yields < DEL_YIELDS && s < t_now && m >= 2 && last_state == ST_TARGET) {
+            if (yields < p.del_yields && s < t_now && m >= 2 && last_state == ST_TARGET) {
                 release_root_word(H, sh, m, s);
                 stat_add(sh, STAT_WAITS, 1);
+                stat_add(sh, STAT_DEL_YIELDS, 1);
                 __nanosleep(512);
                 continue;
             }

@@ -28,7 +28,8 @@ STAT_NAMES = ("node_loads", "node_stores", "merges", "merges_skipped", "ins_ops"
               "del_ops", "lock_waits", "root_hold_ns",
               "del_acquire_cyc", "del_root_step_cyc", "del_child_wait_cyc",
               "del_child_load_cyc", "del_merge_cyc", "del_store_release_cyc", "del_levels",
-              "ins_acquire_cyc", "ins_sort_cyc", "ins_wait_cyc", "ins_step_cyc", "ins_levels")
+              "ins_acquire_cyc", "ins_sort_cyc", "ins_wait_cyc", "ins_step_cyc", "ins_levels",
+              "deliveries", "del_yields")
 
 _lib = None
 
@@ -55,6 +56,7 @@ def lib():
             "heap_destroy": (ctypes.c_int, [vp]),
             "heap_set_launch": (ctypes.c_int, [vp, u32, u32]),
             "heap_set_timeout": (ctypes.c_int, [vp, u64]),
+            "heap_set_yields": (ctypes.c_int, [vp, u32]),
             "heap_insert": (ctypes.c_int, [vp, vp, u64, vp]),
             "heap_delete_min": (ctypes.c_int, [vp, vp, u64, vp, vp]),
             "heap_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, u64, vp]),
@@ -150,6 +152,11 @@ class GHeap:
 
     def set_timeout(self, ns):
         _check(lib().heap_set_timeout(self._h, int(ns)), "heap_set_timeout")
+
+    def set_yields(self, n):
+        """Root hand-backs before a DEL marks an in-flight INS target (0 = the
+        paper's mark-and-wait protocol)."""
+        _check(lib().heap_set_yields(self._h, int(n)), "heap_set_yields")
 
     def _key_tensor(self, t, what):
         if not t.is_cuda:

@@ -170,3 +170,21 @@ def set_phase_ops(sizes, k, kind, base_offsets=None):
     ops["kind_n"] = (int(kind) << 24) | n[order]
     ops["offset"] = (np.asarray(base_offsets)[heap] + j * k)[order]
     return ops
+
+
+def mixed_pairs(n_prefill, n_pairs, k, seed_off=0):
+    """The mixed workload of Section 5.5 (ins-del pairs) in the shape of the
+    raw-heap configuration: `n_prefill` uniform keys to insert first, then an
+    operation list alternating INS and DEL of k keys each, INS j taking keys
+    [j*k, (j+1)*k) of its own uniform stream and DEL j writing to output
+    offset j*k.  Returns (prefill keys, stream keys, ops) with ops a
+    structured array (kind u32, n u32, offset u64), kind 1 = INS, 2 = DEL."""
+    pre = keys_u32(config_seed(2) + 100 + seed_off, n_prefill)
+    stream = keys_u32(config_seed(2) + 200 + seed_off, n_pairs * k)
+    ops = np.zeros(2 * n_pairs, dtype=[("kind", "<u4"), ("n", "<u4"), ("offset", "<u8")])
+    ops["kind"][0::2] = 1
+    ops["kind"][1::2] = 2
+    ops["n"] = k
+    ops["offset"][0::2] = np.arange(n_pairs, dtype=np.uint64) * k
+    ops["offset"][1::2] = np.arange(n_pairs, dtype=np.uint64) * k
+    return pre, stream, ops

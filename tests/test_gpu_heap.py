@@ -159,22 +159,31 @@ def test_ascending_input_never_merges():
         assert np.array_equal(to_host(out, 4), keys)
 
 
+@pytest.mark.parametrize("yields", [64, 0])
 @pytest.mark.parametrize("k,key_bytes,partial", [(1024, 4, False), (1024, 4, True),
                                                   (2048, 4, True), (64, 8, True), (8, 4, True)])
-def test_concurrent_mixed_replay(k, key_bytes, partial):
+def test_concurrent_mixed_replay(k, key_bytes, partial, yields):
     """A prefilled heap under alternating INS/DEL ops from all blocks (the
-    ins-del pairs of Section 5.5); every DEL equals the oracle's replay."""
+    ins-del pairs of Section 5.5); every DEL equals the oracle's replay.
+    yields = 0 is the paper's INS/DEL cooperation (Section 3.3.2): a DEL
+    whose last node is an in-flight INS target marks it and waits for the
+    keys, which the counters must show happened."""
     rng = np.random.default_rng(7 + k)
     prefill = special_keys(rng, 64 * k + 5, key_bytes)
     n_pairs = 512 if k >= 1024 else 2048
     ops, keys, out_size = mixed_ops(rng, n_pairs, k, key_bytes, partial=partial)
     cap = prefill.size + keys.size + k
-    with GHeap(capacity=cap, k=k, key_bytes=key_bytes, log_capacity=4 * n_pairs + 4096) as h:
+    with GHeap(capacity=cap, k=k, key_bytes=key_bytes, log_capacity=4 * n_pairs + 4096,
+               stats=True) as h:
+        h.set_yields(yields)
         r = Recorder(h)
         r.insert(prefill)
         r.ops(ops, keys, out_size)
         assert r.replay_and_compare() >= n_pairs
         check_properties(h)
+        st = h.stats()
+        if yields == 0:
+            assert st["deliveries"] > 0 and st["del_yields"] == 0, st
 
 
 def test_concurrent_drain_from_empty_mixed():

@@ -1,0 +1,61 @@
+"""Config 2's mixed run at full size, replayed through the CPU oracle.
+
+A heap of k = 1024 prefilled with 2^24 uniform uint32 keys takes 2^16
+ins-del pairs of 1024 keys each (Section 5.5) from every thread block of the
+device at once -- the heap is 14 levels deep.  The GPU records the order in
+which operations held the root; replaying that order through the textbook
+binary heap fixes every DEL output (Section 3.3.3, Theorem 1), and every one
+of the 2^16 DELs must match it bit for bit.  Properties 1-3 (Section 3.1)
+must hold on the heap left at the end.  With yields = 0 (the paper's INS/DEL
+cooperation of Section 3.3.2: a DEL whose last node is an INS target still
+in flight marks it and waits, holding the root, for the keys) the device
+counters must show that such deliveries happened at this depth.
+"""
+import numpy as np
+import pytest
+
+from paper_1906_06504_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_06504_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+from heaputil import Recorder, check_properties  # noqa: E402
+
+
+@pytest.mark.parametrize("yields", [64, 0])
+def test_config2_mixed_full_size_replay(yields):
+    from paper_1906_06504_gb300.heap import GHeap
+    n_prefill, n_pairs, k = 1 << 24, 1 << 16, 1024
+    pre, stream, ops = inputs.mixed_pairs(n_prefill, n_pairs, k)
+    log_cap = n_prefill // k + 2 * n_pairs + 1024
+    with GHeap(capacity=n_prefill + n_pairs * k, k=k, log_capacity=log_cap, stats=True) as h:
+        h.set_yields(yields)
+        r = Recorder(h)
+        r.insert(pre)
+        h.sync()
+        before = h.stats()
+        rec = r.ops(ops, stream, n_pairs * k)
+        h.sync()
+        st = h.stats()
+        counts = rec["counts"].cpu().numpy()
+        assert np.all(counts[0::2] == k)
+        # every DEL of the list, each checked against the oracle's replay
+        assert r.replay_and_compare() == n_pairs
+        check_properties(h)
+        deliveries = st["deliveries"] - before["deliveries"]
+        if yields == 0:
+            assert deliveries > 0, st
+        print("yields=%d: %d deliveries, %d root hand-backs, %d DEL levels"
+              % (yields, deliveries, st["del_yields"] - before["del_yields"],
+                 st["del_levels"] - before["del_levels"]))

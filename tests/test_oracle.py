@@ -317,3 +317,16 @@ def test_knapsack_dp_closed_forms():
     assert oracle.knapsack_dp(w, v, 0) == 0         # nothing fits
     assert oracle.knapsack_dp(w, v, 2) == 0
     assert oracle.knapsack_dp(w, v, 8) == 10
+
+
+def test_stl_baseline_sorts_and_reports_its_time():
+    """The std::priority_queue baseline of the paper's Table 1 (timed beside
+    the GPU heap, not used by any check): its push-all/pop-all output is the
+    sorted input, on duplicates and the u32 extremes too."""
+    rng = np.random.default_rng(17)
+    for n in (1, 2, 1000, 65537):
+        keys = rng.integers(0, 2**32, n, dtype=np.uint64).astype(np.uint32)
+        keys[:: max(1, n // 7)] = 0xFFFFFFFF
+        keys[1:: max(1, n // 5)] = 0
+        out, dt = oracle.stl_insert_delete(keys)
+        assert np.array_equal(out, np.sort(keys)) and dt >= 0.0
