@@ -74,6 +74,20 @@ def measured_traffic(kind, n, k, ctas, bottom_up):
     return MEASURED_TRAFFIC[kind]
 
 
+def roofline_of(bytes_moved, ms, kernel, what):
+    """Roofline object for `bytes_moved` algorithmic bytes in `ms`."""
+    peak, kind = peaks()
+    achieved = bytes_moved / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": kind, "algorithmic_bytes": int(bytes_moved),
+            "kernel": kernel, "bytes": what}
+
+
+def node_bytes(st, k, key_bytes):
+    """Node batches loaded and stored, as counted by the kernel."""
+    return (st["node_loads"] + st["node_stores"]) * k * key_bytes
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -183,16 +197,14 @@ def _cpu_full_worker(args):
 class CpuBaselines:
     """The sequential CPU heaps -- the oracle's binary heap and the paper's
     std::priority_queue baseline (Table 1) -- timed on the full workload, best
-    of `reps` runs each.  Every run is a spawn-started worker process on its
-    own host core; they all run at once, while the GPU benchmark does (the
-    host has 16 cores; a run shares only the memory system with the others)."""
+    of `reps` runs each, one after another in a spawn-started worker process
+    per heap (one host core each), while the GPU benchmark runs."""
 
     def __init__(self, n, seed, reps=3):
         import multiprocessing as mp
         self.n, self.reps = n, reps
-        self.pool = mp.get_context("spawn").Pool(2 * reps)
-        self.res = {kind: [self.pool.apply_async(_cpu_full_worker, ((kind, n, 1, seed),))
-                           for _ in range(reps)]
+        self.pool = mp.get_context("spawn").Pool(2)
+        self.res = {kind: [self.pool.apply_async(_cpu_full_worker, ((kind, n, reps, seed),))]
                     for kind in ("oracle", "stl")}
 
     def result(self, timeout=1800):
@@ -201,9 +213,9 @@ class CpuBaselines:
         self.pool.join()
         n = self.n
         what = ("the full workload: insert-all + deleteMin-all of the same %d uniform u32 keys "
-                "(one sequential heap, one thread), best of %d runs; each run a worker process "
-                "on its own host core, all %d runs at once, while the GPU benchmark runs"
-                % (n, self.reps, 2 * self.reps))
+                "(one sequential heap, one thread), best of %d runs one after another in a "
+                "worker process on its own host core, beside the other CPU heap's worker, "
+                "while the GPU benchmark runs" % (n, self.reps))
         return {"value": 2.0 * n / min(runs["oracle"]), "unit": UNIT, "cores": 1,
                 "kind": "oracle", "host": host_cpu(), "sample": what, "same_config": True,
                 "runs_s": runs["oracle"], "build": "gcc -O3",
@@ -356,7 +368,7 @@ def replay_ops_record(log, pre, stream, ops, out, counts, k):
 
 
 def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, seed_off=0,
-              replay=True):
+              replay=True, count=True):
     """Mixed concurrent workload: prefill 2^24 keys, then 2^16 ins-del pairs
     of k keys issued to all blocks at once (Section 5.5 ins-del pairs).  The
     timed launch keeps its linearization record, which the CPU oracle then
@@ -397,6 +409,19 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
         r["exact"] = bool(ok and checked == n_pairs)
         r["dels_checked"] = checked
         r["cpu_oracle_replay_s"] = dt
+    if count:
+        with GHeap(capacity=n_prefill + n_pairs * k, k=k) as h:
+            h.set_launch(ctas=ctas, items_per_thread=ipt)
+            h.insert(d_pre)
+            h.sync()
+            h.set_stats(True)
+            h.ops(d_ops, d_in, d_out, counts)
+            h.sync()
+            st = h.stats()
+        r["roofline"] = roofline_of(node_bytes(st, k, 4) + moved * 4, ms,
+                                    "heap_kernel (operation-list launch)",
+                                    "node batches loaded + stored (kernel counters, separate "
+                                    "run) + the keys inserted and returned")
     return r
 
 
@@ -450,37 +475,70 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_u
             assert np.array_equal(np.sort(out[seg]), np.sort(keys[seg]))
         g_ins.close()
         g_del.close()
+    # node traffic of one step, counted by the kernel in a separate run
+    with GHeapSet([int(x) for x in sizes], k=k, bottom_up=bottom_up, stats=True) as hs:
+        hs.set_launch(items_per_thread=ipt)
+        hs.ops(d_ins, d_keys, None)
+        hs.ops(d_del, None, d_out)
+        torch.cuda.synchronize()
+        st = hs.stats()
+    step_bytes = node_bytes(st, k, 4) + 2 * total * 4
     cpu_v, cores, cpu_s = cpu_oracle_heapset(sizes, keys)
     return {"workload": "256 heaps, log-uniform 2^10..2^22 keys (%d total), insert-all + "
                         "deleteMin-all, one launch each, CUDA-graph replay" % total,
             "insert": "bottom-up" if bottom_up else "top-down",
             "value": 2.0 * total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "k": k, "items_per_thread": ipt, "autotune": table,
+            "roofline": roofline_of(step_bytes, ms, "heap_kernel (heap-set insert + deleteMin "
+                                    "launches)", "node batches loaded + stored (kernel "
+                                    "counters, separate run) + input and output keys"),
             "cpu_oracle": {"value": cpu_v, "unit": UNIT, "cores": cores, "seconds": cpu_s,
                            "host": host_cpu(),
                            "sample": "the same 256 heaps scaled to 1/16 of their sizes, one "
                                      "oracle binary heap each, spread over every host core"}}
 
 
-def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256):
-    """Served heaps: Poisson arrivals of insert / deleteMin
-    requests of 1..4096 keys over 256 heaps, continuously batched."""
+def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256, count=True):
+    """Served heaps: Poisson arrivals of insert / deleteMin requests of
+    1..4096 keys over 256 heaps, continuously batched through one persistent
+    serving launch.  A second, untimed run of the same requests with the
+    kernel's counters on gives the node traffic: each heap takes its requests
+    in arrival order in both runs, so each heap sees the same operations."""
     from paper_1906_06504_gb300 import inputs
     from paper_1906_06504_gb300.serve import HeapServer, latency_summary, poisson_requests
     sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
     caps = [int(max(s, 1 << 18)) for s in sizes]
-    reqs = poisson_requests(inputs.config_seed(5) + 7, n_requests, n_heaps, rate, max_keys=4096)
-    srv = HeapServer(caps, k=1024, max_batch_keys=1 << 22)
-    try:
-        srv.preadmit(range(n_heaps))
-        srv.run(reqs, realtime=True)
-        stats = dict(srv.stats)
-    finally:
-        srv.close()
+
+    def serve(stats, realtime):
+        reqs = poisson_requests(inputs.config_seed(5) + 7, n_requests, n_heaps, rate,
+                                max_keys=4096)
+        srv = HeapServer(caps, k=1024, arena_keys=1 << 24, stats=stats)
+        try:
+            srv.preadmit(range(n_heaps))
+            srv.run(reqs, realtime=realtime)
+            info = dict(srv.stats)
+            if stats:
+                info["counters"] = srv.set.stats()
+        finally:
+            srv.close()
+        return reqs, info
+
+    reqs, info = serve(False, True)
     summ = latency_summary(reqs)
-    summ.update({"arrival_rate_per_s": rate, "heaps": n_heaps, "batches": stats["batches"],
+    summ.update({"arrival_rate_per_s": rate, "heaps": n_heaps,
+                 "max_in_flight": info["max_inflight"],
+                 "submitted_while_busy": info["submitted_while_busy"],
+                 "refused": info["refused"],
                  "workload": "Poisson arrivals, 1..4096 keys, 50/50 insert/deleteMin, "
-                             "256 heaps, k=1024"})
+                             "256 heaps, k=1024, one persistent serving launch"})
+    if count:
+        _, cinfo = serve(True, False)
+        span_s = summ["keys"] / summ["keys_per_s"]
+        summ["roofline"] = roofline_of(
+            node_bytes(cinfo["counters"], 1024, 4), span_s * 1e3,
+            "heap_kernel (serving launch)", "node batches loaded + stored (kernel counters, "
+            "untimed run of the same requests) over the served span; request keys move "
+            "between pinned host memory and the GPU over the host link, not counted")
     return summ
 
 
@@ -537,12 +595,30 @@ def run_apps(torch):
              torch.from_numpy(w.view(np.int32)).cuda())
         with SSSP(rowptr.size - 1, col.size, k=k, batch=batch) as sp:
             ms, (dist, st) = _timed(torch, lambda: sp.run(*d))
+            # node traffic of one run, counted by the kernel (separate run)
+            hp = sp.heap()
+            c0 = hp.stats()
+            hp.set_stats(True)
+            sp.run(*d)
+            hp.set_stats(False)
+            c1 = hp.stats()
         exact = bool(np.array_equal(dist.cpu().numpy().view(np.uint32), want))
         assert exact
         keys = st["keys_deleted"] + st["keys_inserted"]
+        cnt = {a: c1[a] - c0[a] for a in c1}
+        # graph and queue traffic of the relaxation kernels: per visited
+        # vertex its row pointers, per scanned edge (col, w) and the distance,
+        # per lowering the atomic, the insert-buffer write and read, per
+        # deleted key the delete-buffer write and read
+        app_b = (st["visited"] * 16 + st["edges"] * 12 + st["keys_inserted"] * 20
+                 + st["keys_deleted"] * 16)
         res[name] = {"ms": ms, "heap_keys_per_s": keys / (ms / 1e3), "k": k, "batch": batch,
                      "vertices": int(rowptr.size - 1), "edges": int(col.size), "exact": exact,
                      "cpu_oracle_ms": cpu_ms, "cpu_oracle": "textbook Dijkstra, binary heap, 1 core",
+                     "roofline": roofline_of(node_bytes(cnt, k, 8) + app_b, ms,
+                                             "heap_kernel + sssp_relax kernels",
+                                             "heap node batches (kernel counters, separate run) "
+                                             "+ graph and queue traffic of the relaxations"),
                      **st}
     for n, k, batch in ((100, 1024, 65536), (200, 2048, 16384)):
         w, v, cap = inputs.knapsack_instance(n, inputs.config_seed(4))
@@ -554,12 +630,28 @@ def run_apps(torch):
         with Knapsack(n, k=k, batch=batch) as ks:
             ks.set_launch(items_per_thread=16 if k >= 2048 else 8)
             ms, st = _timed(torch, lambda: ks.run(dw, dv, cap))
+            hp = ks.heap()
+            c0 = hp.stats()
+            hp.set_stats(True)
+            ks.run(dw, dv, cap)
+            hp.set_stats(False)
+            c1 = hp.stats()
         assert st["best"] == want
         keys = st["keys_deleted"] + st["keys_inserted"]
+        cnt = {a: c1[a] - c0[a] for a in c1}
+        # per expanded node its pool record read and two children written,
+        # per heap key the delete/insert buffer write and read
+        app_b = st["explored"] * 48 + keys * 16
         res["knapsack_n%d" % n] = {"ms": ms, "heap_keys_per_s": keys / (ms / 1e3), "k": k,
                                    "batch": batch, "capacity": cap, "exact": True,
                                    "cpu_oracle_ms": cpu_ms,
-                                   "cpu_oracle": "textbook O(n*C) dynamic program, 1 core", **st}
+                                   "cpu_oracle": "textbook O(n*C) dynamic program, 1 core",
+                                   "roofline": roofline_of(node_bytes(cnt, k, 8) + app_b, ms,
+                                                           "heap_kernel + ks_expand kernels",
+                                                           "heap node batches (kernel counters, "
+                                                           "separate run) + node pool and "
+                                                           "buffer traffic"),
+                                   **st}
     return res
 
 
@@ -687,15 +779,16 @@ def sweep_levels(torch, k=1024, ipt=8, pairs=1 << 14):
     `pairs` ins-del pairs of k keys from all blocks."""
     for L in (6, 8, 10, 12, 14, 16, 18):
         pre = ((1 << L) - 1) * k
-        r = run_mixed(torch, n_prefill=pre, n_pairs=pairs, k=k, ipt=ipt, seed_off=L)
+        r = run_mixed(torch, n_prefill=pre, n_pairs=pairs, k=k, ipt=ipt, seed_off=L,
+                      count=False)
         yield {"sweep": "levels", "levels": L, "prefill_keys": pre, "pairs": pairs,
                "ms": r["ms"], "keys_per_s": r["value"]}
 
 
 def sweep_serve(torch, n_requests=20000):
     """Serving: arrival rate swept up to saturation; p50/p99 latency."""
-    for rate in (10000.0, 25000.0, 50000.0, 100000.0, 200000.0, 400000.0):
-        r = run_serve(torch, n_requests=n_requests, rate=rate)
+    for rate in (10000.0, 50000.0, 100000.0, 200000.0, 300000.0, 400000.0, 800000.0):
+        r = run_serve(torch, n_requests=n_requests, rate=rate, count=False)
         r["sweep"] = "serve_rate"
         yield r
 
@@ -846,7 +939,8 @@ def run_gpu(args):
     if not args.skip_extras:
         extras["mixed"] = run_mixed(torch, ipt=args.ipt)
         extras["batched"] = run_batched(torch, tune=not args.no_tune)
-        extras["serve"] = run_serve(torch)
+        extras["serve"] = {"low_load": run_serve(torch, rate=50000.0),
+                           "near_saturation": run_serve(torch, rate=200000.0)}
         extras["other_variant"] = run_variant(torch, not bottom_up, ipt=args.ipt)
         extras["apps"] = run_apps(torch)
     cpu = cpu_jobs.result() if cpu_jobs is not None else None
@@ -883,6 +977,9 @@ def run_gpu(args):
         line.update(extras)
         if "batched" in extras:
             line["batched"]["vs_plain"] = extras["batched"]["value"] / value
+        if "serve" in extras:
+            sat = line["serve"]["near_saturation"]
+            sat["vs_plain"] = sat["keys_per_s"] / value
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

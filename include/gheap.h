@@ -109,6 +109,11 @@ int heap_set_launch(gheap_t h, uint32_t ctas, uint32_t items_per_thread);
  * out sets the sticky GHEAP_ERR_TIMEOUT and the kernel returns. */
 int heap_set_timeout(gheap_t h, uint64_t ns);
 
+/* Turns the device counters of heap_get_stats on or off for later launches
+ * (GHEAP_FLAG_STATS at creation turns them on from the start).  Counting
+ * costs time: a run that counts is not a timed run. */
+int heap_set_stats(gheap_t h, uint32_t on);
+
 /* INS/DEL cooperation (Section 3.3.2): a DEL whose last node is the target of
  * an INS still on its way down may mark that target and wait, holding the
  * root, until the INS delivers its keys there -- the paper's protocol, n = 0.
@@ -301,6 +306,90 @@ int heapset_graph_create(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops,
                          gheapset_graph_t *out);
 int heapset_graph_launch(gheapset_graph_t g, void *stream);
 int heapset_graph_destroy(gheapset_graph_t g);
+
+/* ------------------------------------------------------------------------
+ * Serving ring: continuous batching over a heap set.
+ *
+ * One persistent launch serves insert and deleteMin requests on the heaps of
+ * a set while the host keeps adding requests.  The requests, their input keys
+ * and their results live in pinned host memory that the GPU reads and writes
+ * directly (coherently over NVLink-C2C on a Grace host, over PCIe elsewhere):
+ * the host appends a request's operations to a ring and publishes the ring's
+ * tail with one release store; the launch's thread blocks take operations in
+ * ring order as soon as they are published, so a request that arrives while
+ * others run starts at once and runs beside them; the block that finishes a
+ * request's last operation writes its completion record to host memory.
+ * Every heap takes its requests in submission order: the host numbers each
+ * heap's operations with that heap's root tickets (Section 3.3.3's root lock
+ * order), so whichever blocks pick them up, they hold the root in that order
+ * and each result is the one the same requests give one call at a time.  A
+ * DEL whose last node is an INS target still in flight marks it and waits
+ * for the keys (Section 3.3.2; heap_set_yields does not apply here).
+ *
+ * Requests: an insert of n >= 1 keys (ceil(n/k) INS operations) or a
+ * deleteMin of up to n >= 1 keys (ceil(n/k) DEL operations whose results
+ * fill one contiguous, ascending output).  Any number of requests may be in
+ * flight per heap, up to the ring's limits.  Heaps of the set must be driven
+ * only through the ring while it runs, and no other launch on the set may
+ * overlap it.  Heap memory must not be freed (heapset_unbind, heap_destroy)
+ * while the ring runs: stop it first.
+ * ------------------------------------------------------------------------ */
+typedef struct gheap_ring_s *gheap_ring_t;
+
+/* A ring over `set` with room for max_requests requests in flight,
+ * max_ops operation entries (rounded up to a power of two), in_keys input
+ * keys and out_keys output keys (all in pinned host memory; the set's key
+ * width).  Reads each bound heap's next root ticket (synchronizes).  The
+ * ring is not running until heapring_start. */
+int heapring_create(gheap_ring_t *out, gheapset_t set, uint32_t max_requests,
+                    uint64_t max_ops, uint64_t in_keys, uint64_t out_keys);
+
+/* Stops the launch if it runs (heapring_stop) and frees the ring. */
+int heapring_destroy(gheap_ring_t r);
+
+/* After heapset_bind of heap i while the ring is stopped or running: reads
+ * that heap's next root ticket (synchronizes a private stream only). */
+int heapring_attach(gheap_ring_t r, uint32_t i);
+
+/* Launches the persistent serving kernel on the ring's own stream (a no-op
+ * when it runs).  It runs until heapring_stop; a launch that receives no
+ * operation for 10 s ends with an error that heapring_stop reports. */
+int heapring_start(gheap_ring_t r);
+
+/* Asks the launch to end once every published operation has run, and waits
+ * for it.  Returns GHEAP_ERR_TIMEOUT when the launch ended on its idle bound. */
+int heapring_stop(gheap_ring_t r);
+
+/* Appends up to n_req requests: heap index, kind (GHEAP_OP_INS or
+ * GHEAP_OP_DEL) and size per request; `keys` (host memory) holds the insert
+ * requests' keys back to back, in request order.  The keys are copied, so
+ * the caller may reuse `keys` on return.  Each accepted request's id goes to
+ * ids[i].  Returns how many requests were accepted (in order; fewer when the
+ * ring, an arena or the request slots are full: poll, take and retry), or
+ * GHEAP_ERR_ARG for a malformed first request (an empty heap slot, n = 0).
+ * The requests are published before the call returns. */
+int heapring_submit(gheap_ring_t r, uint32_t n_req, const uint32_t *heaps, const uint32_t *kinds,
+                    const uint64_t *sizes, const void *keys, uint64_t *ids);
+
+/* Reports up to `max` requests that completed since they were submitted and
+ * were not reported before: ids, counts (insert: n; deleteMin: keys
+ * returned) and status (GHEAP_OK, or the sticky device error of the heap
+ * that failed an operation of the request).  Does not wait. */
+int heapring_poll(gheap_ring_t r, uint64_t *ids, uint64_t *counts, int32_t *status, uint32_t max,
+                  uint32_t *n_done);
+
+/* Takes n completed requests: their deleteMin keys (each request's keys
+ * ascending) are copied to host_out back to back in the order of ids (at
+ * most cap keys in all), counts[i] = the keys request ids[i] returned (0 for
+ * an insert), and the requests' slots and arena space are freed.  Every
+ * completed request must be taken once.  GHEAP_ERR_ARG (nothing further
+ * taken) for an id that is not completed or already taken, or when cap is
+ * too small. */
+int heapring_take(gheap_ring_t r, uint32_t n, const uint64_t *ids, void *host_out, uint64_t cap,
+                  uint64_t *counts);
+
+/* Requests submitted and not yet taken. */
+int heapring_pending(gheap_ring_t r, uint64_t *in_flight);
 
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is an

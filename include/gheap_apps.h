@@ -59,6 +59,10 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k,
                 uint32_t batch, uint64_t heap_capacity);
 int sssp_destroy(sssp_t s);
 
+/* The context's heap (owned by the context), e.g. for heap_get_stats after
+ * heap_set_stats; NULL for a NULL context. */
+gheap_t sssp_heap(sssp_t s);
+
 /* Launch shape of the heap operations (see heap_set_launch). */
 int sssp_set_launch(sssp_t s, uint32_t ctas, uint32_t items_per_thread);
 
@@ -116,6 +120,9 @@ typedef struct {
 int knapsack_create(knapsack_t *out, uint32_t max_items, uint64_t max_nodes, uint32_t k,
                     uint32_t batch, uint64_t gc_threshold);
 int knapsack_destroy(knapsack_t s);
+
+/* The context's heap (owned by the context); NULL for a NULL context. */
+gheap_t knapsack_heap(knapsack_t s);
 int knapsack_set_launch(knapsack_t s, uint32_t ctas, uint32_t items_per_thread);
 
 /* Solves one instance on `stream` and returns when done (synchronizes).

@@ -4,7 +4,7 @@ import ctypes
 
 import numpy as np
 
-from .heap import _check, _stream_ptr, lib
+from .heap import GHeap, _check, _stream_ptr, lib
 
 SSSP_STATS_DTYPE = np.dtype([("iterations", "<u8"), ("keys_deleted", "<u8"), ("visited", "<u8"),
                              ("edges", "<u8"), ("keys_inserted", "<u8")])
@@ -29,6 +29,10 @@ class SSSP:
 
     def set_launch(self, ctas=0, items_per_thread=8):
         _check(lib().sssp_set_launch(self._h, int(ctas), int(items_per_thread)), "sssp_set_launch")
+
+    def heap(self):
+        """The context's heap, not owned (for its counters)."""
+        return GHeap(0, _handle=lib().sssp_heap(self._h))
 
     def run(self, rowptr, col, w, source=0, dist=None, stream=None):
         """Distances from `source` over the CSR graph (CUDA tensors: rowptr
@@ -84,6 +88,10 @@ class Knapsack:
     def set_launch(self, ctas=0, items_per_thread=8):
         _check(lib().knapsack_set_launch(self._h, int(ctas), int(items_per_thread)),
                "knapsack_set_launch")
+
+    def heap(self):
+        """The context's heap, not owned (for its counters)."""
+        return GHeap(0, _handle=lib().knapsack_heap(self._h))
 
     def run(self, w, v, capacity, stream=None):
         """w, v: int32 CUDA tensors (uint32 bit patterns) of the items.

@@ -332,6 +332,13 @@ int heap_set_timeout(gheap_t h, uint64_t ns)
     return GHEAP_OK;
 }
 
+int heap_set_stats(gheap_t h, uint32_t on)
+{
+    if (!h) return GHEAP_ERR_ARG;
+    h->flags = on ? (h->flags | GHEAP_FLAG_STATS) : (h->flags & ~GHEAP_FLAG_STATS);
+    return GHEAP_OK;
+}
+
 int heap_set_yields(gheap_t h, uint32_t n)
 {
     if (!h) return GHEAP_ERR_ARG;
@@ -1005,6 +1012,403 @@ int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n)
         return GHEAP_ERR_CUDA;
     for (uint32_t i = 0; i < n; i++) out[i] = tmp[i];
     return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// serving ring: one persistent launch over a heap set, fed from host memory
+// ---------------------------------------------------------------------------
+
+namespace {
+
+enum : uint8_t { RQ_FREE = 0, RQ_INFLIGHT = 1, RQ_DONE = 2, RQ_TAKEN = 3 };
+
+struct RingReq {
+    uint64_t seq;
+    uint64_t op_end;                 // ring position after its last op
+    uint64_t in_start, in_end;       // input-arena positions (INS)
+    uint64_t out_start, out_end;     // output-arena positions (DEL)
+    uint64_t n;
+    uint32_t heap;
+    uint32_t kind;
+    uint8_t state;
+};
+
+// Contiguous space of n units in a circular arena of `cap` units whose
+// allocations are freed in order: returns the start position (monotonic),
+// skipping the arena's end when the chunk would wrap, or UINT64_MAX.
+uint64_t arena_take(uint64_t &tail, uint64_t freed, uint64_t cap, uint64_t n)
+{
+    uint64_t pos = tail;
+    if (pos % cap + n > cap) pos = (pos / cap + 1) * cap;
+    if (pos + n - freed > cap) return UINT64_MAX;
+    tail = pos + n;
+    return pos;
+}
+
+template <typename T>
+bool host_map(T **h, T **d, size_t count)
+{
+    if (cudaHostAlloc((void **)h, count * sizeof(T), cudaHostAllocMapped) != cudaSuccess) {
+        *h = nullptr;
+        return false;
+    }
+    memset(*h, 0, count * sizeof(T));
+    return cudaHostGetDevicePointer((void **)d, *h, 0) == cudaSuccess;
+}
+
+}  // namespace
+
+struct gheap_ring_s {
+    gheapset_t set;
+    int device;
+    uint32_t n_slots;
+    uint64_t op_cap, in_cap, out_cap;         // ring entries, arena keys
+    cudaStream_t stream;
+    // pinned host memory, with the device's view of each block
+    gh::RingOp *ops, *d_ops;
+    unsigned long long *tail, *d_tail;
+    uint32_t *stop, *d_stop;
+    gh::RingDone *done, *d_done;
+    uint32_t *req_ops, *d_req_ops;
+    unsigned long long *req_seq, *d_req_seq;
+    unsigned long long *req_base, *d_req_base;
+    unsigned char *in_keys, *d_in_keys;
+    unsigned char *out_keys, *d_out_keys;
+    // device memory
+    uint32_t *d_ops_done, *d_status, *d_err;
+    unsigned long long *d_cursor;
+    gh::Ctl *d_ctl;
+    // host bookkeeping
+    RingReq *reqs;
+    uint64_t next_seq, oldest;
+    uint64_t op_tail, op_free, in_tail, in_free, out_tail, out_free;
+    uint64_t consumed;                        // ring positions run by earlier launches
+    uint64_t *heap_ticket;                    // next root ticket per heap
+    bool running;
+    uint64_t idle_ns;
+};
+
+namespace {
+
+int ring_read_ticket(gheap_ring_t r, uint32_t i)
+{
+    gheap_t h = r->set->heaps[i];
+    if (!h) {
+        r->heap_ticket[i] = 0;
+        return GHEAP_OK;
+    }
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return GHEAP_ERR_CUDA;
+    unsigned long long next = 0;
+    cudaError_t e = cudaMemcpyAsync(&next, &h->d_hdr->next, sizeof(next), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    r->heap_ticket[i] = next;
+    return GHEAP_OK;
+}
+
+template <typename K>
+int ring_launch(gheap_ring_t r)
+{
+    gheapset_t S = r->set;
+    gh::Params<K> p;
+    memset(&p, 0, sizeof(p));
+    p.ctl = r->d_ctl;
+    p.stats = (S->flags & GHEAP_FLAG_STATS) ? S->d_stats : nullptr;
+    p.k = S->k;
+    p.mode = gh::MODE_RING;
+    p.call_id = ++S->call_id;
+    p.timeout_ns = S->timeout_ns;
+    p.del_yields = 0;              // tickets are fixed: a DEL waits for its INS
+    p.in = reinterpret_cast<const K *>(r->d_in_keys);
+    p.out = reinterpret_cast<K *>(r->d_out_keys);
+    p.table = static_cast<const gh::HeapView<K> *>(S->d_table);
+    p.n_heaps = S->n;
+    p.req_base = r->d_req_base;
+    p.req_cursor = r->d_cursor;
+    p.ring_ops = r->d_ops;
+    p.ring_cap = r->op_cap;
+    p.ring_base = r->consumed;
+    p.ring_tail = r->d_tail;
+    p.ring_stop = r->d_stop;
+    p.ring_req_ops = r->d_req_ops;
+    p.ring_req_seq = r->d_req_seq;
+    p.ring_done = r->d_done;
+    p.ring_ops_done = r->d_ops_done;
+    p.ring_status = r->d_status;
+    p.ring_err = r->d_err;
+    p.ring_idle_ns = r->idle_ns;
+    Shape sp;
+    sp.k = S->k;
+    sp.ipt = S->ipt;
+    sp.ctas = S->ctas;
+    sp.per_sm_default = 2;
+    sp.sm_count = S->sm_count;
+    sp.d_ctl = r->d_ctl;
+    return launch_k<K>(sp, p, ~0ull, r->stream);
+}
+
+int status_code(uint32_t bits)
+{
+    if (bits & (1u << gh::E_TIMEOUT)) return GHEAP_ERR_TIMEOUT;
+    if (bits & (1u << gh::E_FULL)) return GHEAP_ERR_FULL;
+    if (bits) return GHEAP_ERR_STATE;
+    return GHEAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int heapring_destroy(gheap_ring_t r);
+
+int heapring_create(gheap_ring_t *out, gheapset_t set, uint32_t max_requests,
+                    uint64_t max_ops, uint64_t in_keys, uint64_t out_keys)
+{
+    if (!out || !set || max_requests == 0 || max_ops == 0 || in_keys == 0 || out_keys == 0)
+        return GHEAP_ERR_ARG;
+    *out = nullptr;
+    uint64_t cap = 1;
+    while (cap < max_ops) cap <<= 1;
+    gheap_ring_t r = (gheap_ring_t)calloc(1, sizeof(gheap_ring_s));
+    if (!r) return GHEAP_ERR_OOM;
+    r->set = set;
+    r->device = set->device;
+    r->n_slots = max_requests;
+    r->op_cap = cap;
+    r->in_cap = in_keys;
+    r->out_cap = out_keys;
+    r->idle_ns = 10000000000ull;
+    const size_t kb = set->key_bytes;
+    r->reqs = (RingReq *)calloc(max_requests, sizeof(RingReq));
+    r->heap_ticket = (uint64_t *)calloc(set->n, sizeof(uint64_t));
+    bool ok = r->reqs && r->heap_ticket && cudaSetDevice(r->device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              host_map(&r->ops, &r->d_ops, cap) && host_map(&r->tail, &r->d_tail, 1) &&
+              host_map(&r->stop, &r->d_stop, 1) &&
+              host_map(&r->done, &r->d_done, max_requests) &&
+              host_map(&r->req_ops, &r->d_req_ops, max_requests) &&
+              host_map(&r->req_seq, &r->d_req_seq, max_requests) &&
+              host_map(&r->req_base, &r->d_req_base, max_requests) &&
+              host_map(&r->in_keys, &r->d_in_keys, in_keys * kb) &&
+              host_map(&r->out_keys, &r->d_out_keys, out_keys * kb) &&
+              cudaMalloc((void **)&r->d_ops_done, max_requests * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc((void **)&r->d_status, max_requests * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc((void **)&r->d_err, sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc((void **)&r->d_cursor, max_requests * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc((void **)&r->d_ctl, sizeof(gh::Ctl)) == cudaSuccess;
+    if (ok) {
+        ok = cudaMemsetAsync(r->d_ops_done, 0, max_requests * sizeof(uint32_t), r->stream) == cudaSuccess &&
+             cudaMemsetAsync(r->d_status, 0, max_requests * sizeof(uint32_t), r->stream) == cudaSuccess &&
+             cudaMemsetAsync(r->d_err, 0, sizeof(uint32_t), r->stream) == cudaSuccess &&
+             cudaMemsetAsync(r->d_cursor, 0, max_requests * sizeof(unsigned long long), r->stream) == cudaSuccess &&
+             cudaMemsetAsync(r->d_ctl, 0, sizeof(gh::Ctl), r->stream) == cudaSuccess &&
+             cudaStreamSynchronize(r->stream) == cudaSuccess;
+    }
+    for (uint32_t i = 0; ok && i < set->n; i++) ok = ring_read_ticket(r, i) == GHEAP_OK;
+    if (!ok) {
+        cudaGetLastError();
+        heapring_destroy(r);
+        return GHEAP_ERR_OOM;
+    }
+    *out = r;
+    return GHEAP_OK;
+}
+
+int heapring_attach(gheap_ring_t r, uint32_t i)
+{
+    if (!r || i >= r->set->n) return GHEAP_ERR_ARG;
+    if (cudaSetDevice(r->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    return ring_read_ticket(r, i);
+}
+
+int heapring_start(gheap_ring_t r)
+{
+    if (!r) return GHEAP_ERR_ARG;
+    if (r->running) return GHEAP_OK;
+    if (cudaSetDevice(r->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    __atomic_store_n(r->stop, 0u, __ATOMIC_RELEASE);
+    const int rc = r->set->key_bytes == 4 ? ring_launch<uint32_t>(r) : ring_launch<uint64_t>(r);
+    if (rc == GHEAP_OK) r->running = true;
+    return rc;
+}
+
+int heapring_stop(gheap_ring_t r)
+{
+    if (!r) return GHEAP_ERR_ARG;
+    if (!r->running) return GHEAP_OK;
+    if (cudaSetDevice(r->device) != cudaSuccess) return GHEAP_ERR_CUDA;
+    __atomic_store_n(r->stop, 1u, __ATOMIC_RELEASE);
+    cudaError_t e = cudaStreamSynchronize(r->stream);
+    r->running = false;
+    // every published operation ran before the launch ended
+    r->consumed = r->op_tail;
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    uint32_t err = 0;
+    e = cudaMemcpyAsync(&err, r->d_err, sizeof(err), cudaMemcpyDeviceToHost, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    return err ? GHEAP_ERR_TIMEOUT : GHEAP_OK;
+}
+
+int heapring_submit(gheap_ring_t r, uint32_t n_req, const uint32_t *heaps, const uint32_t *kinds,
+                    const uint64_t *sizes, const void *keys, uint64_t *ids)
+{
+    if (!r || (n_req && (!heaps || !kinds || !sizes))) return GHEAP_ERR_ARG;
+    gheapset_t S = r->set;
+    const uint32_t k = S->k;
+    const size_t kb = S->key_bytes;
+    const unsigned char *src = static_cast<const unsigned char *>(keys);
+    uint32_t i = 0;
+    for (; i < n_req; i++) {
+        const uint32_t h = heaps[i], kind = kinds[i];
+        const uint64_t n = sizes[i];
+        if (h >= S->n || !S->heaps[h] || n == 0 || (kind != GHEAP_OP_INS && kind != GHEAP_OP_DEL) ||
+            (kind == GHEAP_OP_INS && !src))
+            return i ? (int)i : GHEAP_ERR_ARG;
+        if (r->next_seq - r->oldest >= r->n_slots) break;
+        const uint64_t n_ops = (n + k - 1) / k;
+        if (r->op_tail + n_ops - r->op_free > r->op_cap) break;
+        uint64_t in_pos = 0, out_pos = 0;
+        uint64_t in_tail = r->in_tail, out_tail = r->out_tail;
+        if (kind == GHEAP_OP_INS) {
+            in_pos = arena_take(in_tail, r->in_free, r->in_cap, n);
+            if (in_pos == UINT64_MAX) break;
+        } else {
+            out_pos = arena_take(out_tail, r->out_free, r->out_cap, n);
+            if (out_pos == UINT64_MAX) break;
+        }
+        const uint64_t seq = r->next_seq;
+        const uint32_t slot = (uint32_t)(seq % r->n_slots);
+        RingReq &q = r->reqs[slot];
+        q.seq = seq;
+        q.heap = h;
+        q.kind = kind;
+        q.n = n;
+        q.in_start = kind == GHEAP_OP_INS ? in_pos : r->in_tail;
+        q.in_end = in_tail;
+        q.out_start = kind == GHEAP_OP_DEL ? out_pos : r->out_tail;
+        q.out_end = out_tail;
+        r->in_tail = in_tail;
+        r->out_tail = out_tail;
+        r->req_ops[slot] = (uint32_t)n_ops;
+        r->req_seq[slot] = seq;
+        r->req_base[slot] = kind == GHEAP_OP_DEL ? out_pos % r->out_cap : 0;
+        if (kind == GHEAP_OP_INS) {
+            memcpy(r->in_keys + (in_pos % r->in_cap) * kb, src, n * kb);
+            src += n * kb;
+        }
+        for (uint64_t j = 0; j < n_ops; j++) {
+            gh::RingOp &o = r->ops[r->op_tail % r->op_cap];
+            const uint32_t m = (uint32_t)(n - j * k < k ? n - j * k : k);
+            o.heap = h;
+            o.kind_n = (kind << 24) | (kind == GHEAP_OP_DEL ? GHEAPSET_CURSOR : 0u) | m;
+            o.offset = kind == GHEAP_OP_INS ? in_pos % r->in_cap + j * k : slot;
+            o.ticket = r->heap_ticket[h]++;
+            o.req = slot;
+            o._pad = 0;
+            r->op_tail++;
+        }
+        q.op_end = r->op_tail;
+        q.state = RQ_INFLIGHT;
+        r->next_seq++;
+        if (ids) ids[i] = seq;
+    }
+    // publish: every entry and key written above before the new tail
+    __atomic_store_n(r->tail, (unsigned long long)r->op_tail, __ATOMIC_RELEASE);
+    return (int)i;
+}
+
+int heapring_poll(gheap_ring_t r, uint64_t *ids, uint64_t *counts, int32_t *status, uint32_t max,
+                  uint32_t *n_done)
+{
+    if (!r || !n_done || (max && !ids)) return GHEAP_ERR_ARG;
+    uint32_t c = 0;
+    for (uint64_t s = r->oldest; s < r->next_seq && c < max; s++) {
+        const uint32_t slot = (uint32_t)(s % r->n_slots);
+        RingReq &q = r->reqs[slot];
+        if (q.state != RQ_INFLIGHT) continue;
+        if (__atomic_load_n(&r->done[slot].seq, __ATOMIC_ACQUIRE) != s + 1) continue;
+        q.state = RQ_DONE;
+        ids[c] = s;
+        if (counts) counts[c] = q.kind == GHEAP_OP_DEL ? r->done[slot].count : q.n;
+        if (status) status[c] = status_code(r->done[slot].status);
+        c++;
+    }
+    *n_done = c;
+    return GHEAP_OK;
+}
+
+int heapring_take(gheap_ring_t r, uint32_t n, const uint64_t *ids, void *host_out, uint64_t cap,
+                  uint64_t *counts)
+{
+    if (!r || (n && !ids)) return GHEAP_ERR_ARG;
+    const size_t kb = r->set->key_bytes;
+    unsigned char *dst = static_cast<unsigned char *>(host_out);
+    uint64_t used = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        const uint64_t id = ids[i];
+        if (id >= r->next_seq || id < r->oldest) return GHEAP_ERR_ARG;
+        const uint32_t slot = (uint32_t)(id % r->n_slots);
+        RingReq &q = r->reqs[slot];
+        if (q.seq != id || q.state != RQ_DONE) return GHEAP_ERR_ARG;
+        uint64_t cnt = 0;
+        if (q.kind == GHEAP_OP_DEL) {
+            cnt = r->done[slot].count;
+            if (used + cnt > cap || (cnt && !dst)) return GHEAP_ERR_ARG;
+            memcpy(dst + used * kb, r->out_keys + (q.out_start % r->out_cap) * kb, cnt * kb);
+            used += cnt;
+        }
+        if (counts) counts[i] = cnt;
+        q.state = RQ_TAKEN;
+    }
+    // free the arenas, the op entries and the slots of the oldest requests taken
+    while (r->oldest < r->next_seq) {
+        RingReq &o = r->reqs[r->oldest % r->n_slots];
+        if (o.state != RQ_TAKEN) break;
+        r->op_free = o.op_end;
+        if (o.in_end > r->in_free) r->in_free = o.in_end;
+        if (o.out_end > r->out_free) r->out_free = o.out_end;
+        o.state = RQ_FREE;
+        r->oldest++;
+    }
+    return GHEAP_OK;
+}
+
+int heapring_pending(gheap_ring_t r, uint64_t *in_flight)
+{
+    if (!r || !in_flight) return GHEAP_ERR_ARG;
+    *in_flight = r->next_seq - r->oldest;
+    return GHEAP_OK;
+}
+
+int heapring_destroy(gheap_ring_t r)
+{
+    if (!r) return GHEAP_ERR_ARG;
+    heapring_stop(r);
+    cudaSetDevice(r->device);
+    cudaFreeHost(r->ops);
+    cudaFreeHost(r->tail);
+    cudaFreeHost(r->stop);
+    cudaFreeHost(r->done);
+    cudaFreeHost(r->req_ops);
+    cudaFreeHost(r->req_seq);
+    cudaFreeHost(r->req_base);
+    cudaFreeHost(r->in_keys);
+    cudaFreeHost(r->out_keys);
+    cudaFree(r->d_ops_done);
+    cudaFree(r->d_status);
+    cudaFree(r->d_err);
+    cudaFree(r->d_cursor);
+    cudaFree(r->d_ctl);
+    if (r->stream) cudaStreamDestroy(r->stream);
+    free(r->reqs);
+    free(r->heap_ticket);
+    free(r);
+    return GHEAP_OK;
 }
 
 }  // extern "C"

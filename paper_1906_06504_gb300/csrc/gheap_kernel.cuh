@@ -76,7 +76,31 @@ constexpr uint32_t ST_GAVE_UP = ~0u;
 constexpr uint32_t DEL_YIELDS = 64;
 constexpr uint32_t NO_TRY = ~1u;     // "no earlier lock attempt"
 
-enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2, MODE_SET = 3 };
+enum : uint32_t { MODE_INSERT = 0, MODE_DELETE = 1, MODE_OPS = 2, MODE_SET = 3, MODE_RING = 4 };
+
+// MODE_RING: the serving form.  One persistent launch takes its operations
+// from a ring that the host appends to while the launch runs; the ring, the
+// request tables, the input keys and the output keys live in pinned host
+// memory, which the GPU reads and writes directly (NVLink-C2C on a Grace
+// host).  An operation names its heap, its request slot and its root ticket:
+// the host numbers each heap's operations in ring order, so every heap takes
+// its requests in arrival order however the blocks pick them up.
+struct __align__(16) RingOp {
+    uint32_t heap;
+    uint32_t kind_n;              // as gheapset_op (DELs use the request cursor)
+    unsigned long long offset;    // INS: key position in the input arena; DEL: request slot
+    unsigned long long ticket;    // this heap's root ticket for the operation
+    uint32_t req;                 // request slot
+    uint32_t _pad;
+};
+// Completion record of a request slot, written by the block that finishes the
+// request's last operation: count and status first, then seq (release).
+struct __align__(16) RingDone {
+    unsigned long long seq;       // request sequence number + 1 once complete
+    unsigned long long count;     // DEL: keys written; INS: 0
+    uint32_t status;              // 0, or the device error that hit an operation
+    uint32_t _pad[3];
+};
 
 enum : uint32_t { E_NONE = 0, E_TIMEOUT = 1, E_FULL = 2, E_STATE = 3 };
 
@@ -166,6 +190,19 @@ struct HeapView {
     uint32_t _pad;
 };
 
+// Node keys and lock word of storage slot s.
+template <typename K>
+__device__ __forceinline__ K *node_keys(const HeapView<K> &H, uint32_t s, uint32_t k)
+{
+    return H.keys + (size_t)s * k;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t *node_state(const HeapView<K> &H, uint32_t s)
+{
+    return H.state + s;
+}
+
 template <typename K>
 struct Params {
     HeapView<K> h;
@@ -192,6 +229,19 @@ struct Params {
     unsigned long long *req_cursor;       //   and running count, per request
     const unsigned long long *n_dev;      // MODE_INSERT: key count in device memory
     const uint32_t *set_bu;      // MODE_SET: nonzero = the list has no DEL, insert bottom-up
+    // MODE_RING (host memory unless marked device)
+    const RingOp *ring_ops;      // the op ring, ring_cap entries (a power of two)
+    unsigned long long ring_cap;
+    unsigned long long ring_base; // ring position of this launch's first operation
+    const unsigned long long *ring_tail;   // positions published by the host
+    const uint32_t *ring_stop;   // nonzero: leave once every published op is taken
+    const uint32_t *ring_req_ops;          // operations per request slot
+    const unsigned long long *ring_req_seq; // request sequence number per slot
+    RingDone *ring_done;         // completion records per slot
+    uint32_t *ring_ops_done;     // device: operations finished per slot
+    uint32_t *ring_status;       // device: error bits per slot
+    uint32_t *ring_err;          // device: the ring's own error (a wait gave up)
+    unsigned long long ring_idle_ns;       // bound on a wait for new operations
 };
 
 // A hand-off to the release warp: behind one fence, up to two lock words set
@@ -215,6 +265,8 @@ struct Shared {
     unsigned long long t_root;
     uint32_t m, s, take, tslot;
     uint32_t turn;            // root ticket held by this block
+    uint32_t use_fixed;       // MODE_RING: the root ticket is fixed_ticket
+    unsigned long long fixed_ticket;
     int lockfree;             // bottom-up INS: target reserved without the root lock
     int stop;
     int abort;
@@ -330,6 +382,7 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v)
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+
 // Releases (a st.release.gpu, or a fence.acq_rel.gpu and relaxed stores) are
 // issued by one thread after a block barrier that follows the merge threads'
 // stores -- control lane 0 or merge thread 0, or in deleteMin the release
@@ -365,6 +418,8 @@ __device__ __forceinline__ void fence_acq_rel()
 {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
+
+
 
 template <typename K>
 __device__ __forceinline__ K kmax() { return ~K(0); }
@@ -474,8 +529,11 @@ template <typename K>
 __device__ void release_loop(const Params<K> &p, Shared &sh, uint32_t *rel_exited)
 {
     if ((threadIdx.x & 31u) != 0) return;
-    const unsigned long long idle_max =
+    unsigned long long idle_max =
         8ull * p.timeout_ns > 20000000000ull ? 8ull * p.timeout_ns : 20000000000ull;
+    // a serving launch may wait that long for its next operation
+    if (p.mode == MODE_RING && idle_max < p.ring_idle_ns + 10000000000ull)
+        idle_max = p.ring_idle_ns + 10000000000ull;
     for (uint32_t next = 0;; ++next) {
         if (!spin_until(&sh.rq_posted, next + 1, idle_max)) break;
         const RelReq r = sh.rq[next % N_REQ];
@@ -585,7 +643,11 @@ __device__ bool lock_root(const Params<K> &p, const HeapView<K> &H, Shared &sh,
 {
     unsigned long long t0 = 0;
     uint32_t it = 0;
-    const uint32_t ticket = (uint32_t)(atomicAdd(&H.hdr->next, 1ull) & RW_TURN_MASK);
+    // a ring operation's ticket was drawn by the host, in the heap's request
+    // order; the dispenser is advanced past it so that later launches go on
+    const uint32_t ticket =
+        sh.use_fixed ? (uint32_t)(sh.fixed_ticket & RW_TURN_MASK)
+                     : (uint32_t)(atomicAdd(&H.hdr->next, 1ull) & RW_TURN_MASK);
     for (;;) {
         const unsigned long long v = ld_acquire64(&H.hdr->root);
         const uint32_t ahead = (ticket - rw_turn(v)) & (uint32_t)RW_TURN_MASK;
@@ -593,6 +655,9 @@ __device__ bool lock_root(const Params<K> &p, const HeapView<K> &H, Shared &sh,
             if (it) stat_add(sh, STAT_WAITS, 1);
             sh.turn = ticket;
             word = v;
+            if (sh.use_fixed)
+                asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;"
+                             :: "l"(&H.hdr->next), "l"(sh.fixed_ticket + 1ull) : "memory");
             return true;
         }
         if (!wait_ok(p, H, t0, it)) return false;
@@ -1812,7 +1877,7 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
     if (lane < 2) {
         const uint32_t sx = lane ? sr : sl;
         if (sx) {
-            w = &H.state[sx];
+            w = node_state(H, sx);
             const uint32_t f = lane ? first1 : first0;
             v = f == NO_TRY ? try_lock(w) : f;
         }
@@ -1836,8 +1901,8 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
     }
     if (lane < 2) lk[lane] = v;
     __syncwarp();
-    if (lk[0] == ST_AVAIL) g2s(dl, H.keys + (size_t)sl * k, k, lane, 32u);
-    if (lk[1] == ST_AVAIL) g2s(dr, H.keys + (size_t)sr * k, k, lane, 32u);
+    if (lk[0] == ST_AVAIL) g2s(dl, node_keys(H, sl, k), k, lane, 32u);
+    if (lk[1] == ST_AVAIL) g2s(dr, node_keys(H, sr, k), k, lane, 32u);
     cp_async_commit();
     if (lane == 0) stat_add(sh, STAT_LOADS, (lk[0] == ST_AVAIL) + (lk[1] == ST_AVAIL));
     cp_async_wait();
@@ -1856,7 +1921,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     const uint32_t k = p.k;
     const bool ctrl = is_ctrl();
     const uint32_t lane = clane();
-    K *root = H.keys + (size_t)k;
+    K *root = node_keys(H, 1u, k);
     long long tp = clock64();
 #define PB(i) (base + (size_t)(i) * k)
 
@@ -1875,7 +1940,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             // both loads go out before either value is used; a delete-only
             // launch has no insert in flight (earlier launches completed)
             const uint32_t last_state =
-                (p.mode != MODE_DELETE && m >= 2) ? ld_relaxed(&H.state[m]) : ST_AVAIL;
+                (p.mode != MODE_DELETE && m >= 2) ? ld_relaxed(node_state(H, m)) : ST_AVAIL;
             if (p.mode == MODE_DELETE) done = ld_relaxed64(&p.ctl->delivered);
             uint32_t w_now = want;
             if (p.mode == MODE_DELETE) {
@@ -1905,7 +1970,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             } else if (req >= 0) {
                 // one request's DELs fill its output contiguously, in the order
                 // they hold this heap's root
-                out_off = p.req_base[req] + p.req_cursor[req];
+                out_off = __ldcv(p.req_base + req) + p.req_cursor[req];
             }
             const uint32_t avail = m >= 1 ? k : s;
             const uint32_t take = want < avail ? want : avail;
@@ -1972,7 +2037,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         uint32_t sl, sr;
         child_slots(1, H.max_nodes, sl, sr);
         if (need_last) {
-            uint32_t *lw = &H.state[m];
+            uint32_t *lw = node_state(H, m);
             if (m <= 3) {
                 // the last node is a child of the root: take it first, then
                 // lock the other child (the taken one reads EMPTY)
@@ -1981,7 +2046,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     else sh.abort = 1;
                 }
                 __syncwarp();
-                if (!sh.abort) g2s(PB(f1), H.keys + (size_t)m * k, k, lane, 32u);
+                if (!sh.abort) g2s(PB(f1), node_keys(H, m, k), k, lane, 32u);
                 cp_async_commit();
                 cw_take_children(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir), sh.lk[0]);
             } else {
@@ -1990,17 +2055,17 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 // the children are given back while the DEL waits for it.
                 uint32_t t = ST_EMPTY;
                 if (lane == 2) t = try_lock(lw);
-                if (lane < 2) t = try_lock(&H.state[lane ? sr : sl]);
+                if (lane < 2) t = try_lock(node_state(H, lane ? sr : sl));
                 const uint32_t tl = __shfl_sync(0xffffffffu, t, 2);
                 const bool inflight = tl != ST_AVAIL && tl != ST_INUSE;
                 if (inflight && lane < 2 && t == ST_AVAIL)
-                    st_release(&H.state[lane ? sr : sl], ST_AVAIL);
+                    st_release(node_state(H, lane ? sr : sl), ST_AVAIL);
                 if (lane == 2) {
                     if (take_last(p, H, sh, lw, tl)) st_relaxed(lw, ST_EMPTY);
                     else sh.abort = 1;
                 }
                 __syncwarp();
-                if (!sh.abort) g2s(PB(f1), H.keys + (size_t)m * k, k, lane, 32u);
+                if (!sh.abort) g2s(PB(f1), node_keys(H, m, k), k, lane, 32u);
                 cp_async_commit();
                 const uint32_t c0 = __shfl_sync(0xffffffffu, t, 0);
                 const uint32_t c1 = __shfl_sync(0xffffffffu, t, 1);
@@ -2082,8 +2147,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             // one child present (the other is absent or an INS target)
             const bool usel = pl;
             const uint32_t xs = usel ? sl : sr;
-            uint32_t *xw = &H.state[xs];
-            K *xk = H.keys + (size_t)xs * k;
+            uint32_t *xw = node_state(H, xs);
+            K *xk = node_keys(H, xs, k);
             if (cmax <= (usel ? c0 : d0)) {
                 if (ctrl && lane == 0) st_release(xw, ST_AVAIL);
                 break;
@@ -2142,7 +2207,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         // both children present
         if (cmax <= c0 && cmax <= d0) {
             // early stop (Section 4.3)
-            if (ctrl && lane < 2) st_release(&H.state[lane ? sr : sl], ST_AVAIL);
+            if (ctrl && lane < 2) st_release(node_state(H, lane ? sr : sl), ST_AVAIL);
             break;
         }
         // MergeAndSort(l, r): the k largest go to the child whose maximum was
@@ -2166,10 +2231,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         K *const S = S_is_C ? C : D;
         K *const L = S_is_C ? D : C;
         const uint32_t bigs = big_l ? sl : sr, sms = big_l ? sr : sl;
-        K *big_keys = H.keys + (size_t)bigs * k;
-        K *sm_keys = H.keys + (size_t)sms * k;
-        uint32_t *big_w = &H.state[bigs];
-        uint32_t *sm_w = &H.state[sms];
+        K *big_keys = node_keys(H, bigs, k);
+        K *sm_keys = node_keys(H, sms, k);
+        uint32_t *big_w = node_state(H, bigs);
+        uint32_t *sm_w = node_state(H, sms);
         const bool big_changed = big_l ? l_changed : r_changed;
         const bool sm_changed = big_l ? r_changed : l_changed;
         if (split_form) {
@@ -2243,8 +2308,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 if (ctrl && lane == 0) {
                     st_release(big_w, ST_AVAIL);
                     st_release(sm_w, ST_AVAIL);
-                    if (gl && sh.lk[par ^ 1][0] == ST_AVAIL) st_release(&H.state[gl], ST_AVAIL);
-                    if (gr && sh.lk[par ^ 1][1] == ST_AVAIL) st_release(&H.state[gr], ST_AVAIL);
+                    if (gl && sh.lk[par ^ 1][0] == ST_AVAIL) st_release(node_state(H, gl), ST_AVAIL);
+                    if (gr && sh.lk[par ^ 1][1] == ST_AVAIL) st_release(node_state(H, gr), ST_AVAIL);
                 }
                 break;
             }
@@ -2285,7 +2350,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         } else if (lane < 2) {
             // try the small child's children while the merge threads work
             const uint32_t gx = lane ? gr : gl;
-            if (gx) t_try = try_lock(&H.state[gx]);
+            if (gx) t_try = try_lock(node_state(H, gx));
         }
         bar_all();
         const bool halt = sh.halt;
@@ -2300,7 +2365,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 if (halt) {
                     // the sift ends here: give back what the tries took
                     if (lane < 2 && t_try == ST_AVAIL)
-                        st_release(&H.state[lane ? gr : gl], ST_AVAIL);
+                        st_release(node_state(H, lane ? gr : gl), ST_AVAIL);
                 } else {
                     long long tw = clock64();
                     const uint32_t t0 = __shfl_sync(0xffffffffu, t_try, 0);
@@ -2390,6 +2455,100 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
 }
 
 // ---------------------------------------------------------------------------
+// the serving ring (MODE_RING)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_sys32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_sys64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.sys.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// Thread 0: waits until ring position `pos` is published.  False: the host
+// asked the launch to stop and `pos` was never published, or no operation
+// came for ring_idle_ns (the ring's error word is then set).  The stop flag
+// is read with acquire and the tail once more after it, so that an operation
+// published before the stop is never left behind.
+template <typename K>
+__device__ bool ring_wait(const Params<K> &p, unsigned long long pos)
+{
+    unsigned long long t0 = 0;
+    for (uint32_t it = 1;; ++it) {
+        unsigned long long tail = ld_acquire_sys64(p.ring_tail);
+        if (pos < tail) return true;
+        if (ld_acquire_sys32(p.ring_stop)) {
+            tail = ld_acquire_sys64(p.ring_tail);
+            return pos < tail;
+        }
+        if ((it & 15u) == 0) {
+            const unsigned long long now = gtimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > p.ring_idle_ns) {
+                atomicExch(p.ring_err, 1u);
+                return false;
+            }
+            if (ld_relaxed(p.ring_err)) return false;
+        }
+        // the next position to be published polls often, the ones behind it less
+        const unsigned long long ahead = pos - tail;
+        __nanosleep(ahead < 2 ? 64u : (ahead < 64 ? 512u : 2048u));
+    }
+}
+
+// One ring operation, read from host memory (fresh: the entry is reused).
+__device__ __forceinline__ RingOp ld_ring_op(const RingOp *e)
+{
+    const uint4 a = __ldcv(reinterpret_cast<const uint4 *>(e));
+    const uint4 b = __ldcv(reinterpret_cast<const uint4 *>(e) + 1);
+    RingOp d;
+    d.heap = a.x;
+    d.kind_n = a.y;
+    d.offset = (unsigned long long)a.z | ((unsigned long long)a.w << 32);
+    d.ticket = (unsigned long long)b.x | ((unsigned long long)b.y << 32);
+    d.req = b.z;
+    d._pad = b.w;
+    return d;
+}
+
+// Thread 0, after a barrier that follows every store of the block's
+// operation: counts the operation done for its request; the block that
+// finishes a request's last operation writes the completion record (count
+// and status, then the sequence number with release) to host memory and
+// clears the slot's device counters for its next request.
+template <typename K>
+__device__ void ring_complete(const Params<K> &p, uint32_t req, uint32_t status)
+{
+    __threadfence_system();   // the operation's output reaches the host first
+    if (status) atomicOr(p.ring_status + req, status);
+    const uint32_t n_ops = __ldcv(p.ring_req_ops + req);
+    const uint32_t done = atomicAdd(p.ring_ops_done + req, 1u) + 1u;
+    if (done != n_ops) return;
+    __threadfence();          // the other operations' cursor updates are seen
+    const unsigned long long cnt = p.req_cursor[req];
+    const uint32_t st = atomicExch(p.ring_status + req, 0u);
+    p.req_cursor[req] = 0;
+    p.ring_ops_done[req] = 0;
+    RingDone *r = p.ring_done + req;
+    r->count = cnt;
+    r->status = st;
+    st_release_sys64(&r->seq, __ldcv(p.ring_req_seq + req) + 1ull);
+}
+
+// ---------------------------------------------------------------------------
 // persistent kernel
 // ---------------------------------------------------------------------------
 
@@ -2419,8 +2578,10 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
     __shared__ unsigned long long set_off;
     const uint32_t k = p.k;
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
-    const bool multi = !DEL_ONLY && p.mode == MODE_SET;
+    const bool ring = !DEL_ONLY && p.mode == MODE_RING;
+    const bool multi = !DEL_ONLY && (p.mode == MODE_SET || ring);
     const HeapView<K> &H = multi ? set_view : p.h;
+    __shared__ uint32_t ring_req;      // MODE_RING: request slot of the current op
     // a heap-set launch holding only inserts inserts bottom-up (no DEL can
     // meet a rising batch, and every heap's node count only grows)
     const bool set_bu = multi && p.set_bu != nullptr && *p.set_bu != 0u;
@@ -2430,6 +2591,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         sh.rq_posted = 0;
         sh.rq_read = 0;
         sh.stats_on = p.stats != nullptr;
+        sh.use_fixed = 0;
         rel_exited = 0;
     }
     bar_block();
@@ -2450,11 +2612,28 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned long long op = atomicAdd(&p.ctl->next_op, 1ull);
+            int stop;
+            gheapset_op d = {};
+            if (ring) {
+                // the next ring position, once the host has published it
+                op += p.ring_base;
+                stop = !ring_wait(p, op);
+                if (!stop) {
+                    const RingOp e = ld_ring_op(p.ring_ops + (op & (p.ring_cap - 1ull)));
+                    d.heap = e.heap;
+                    d.kind_n = e.kind_n;
+                    d.offset = e.offset;
+                    sh.use_fixed = 1;
+                    sh.fixed_ticket = e.ticket;
+                    ring_req = e.req;
+                }
+            } else {
+                stop = op >= n_ops;
+                if (!stop && multi) d = p.sops[op];
+            }
             sh.op = op;
-            int stop = op >= n_ops;
             if (!stop && multi) {
                 // the op names its heap; a heap with a sticky error skips it
-                const gheapset_op d = p.sops[op];
                 const uint32_t hid = d.heap < p.n_heaps ? d.heap : 0u;
                 set_view = p.table[hid];
                 set_kind = d.kind_n >> 24;
@@ -2499,6 +2678,10 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         } else if (multi) {
             if (set_skip) {
                 if (threadIdx.x == 0 && p.out_counts) p.out_counts[op] = 0;
+                if (ring && threadIdx.x == 0) {
+                    const uint32_t e = set_view.hdr ? ld_relaxed(&set_view.hdr->err) : E_STATE;
+                    ring_complete(p, ring_req, 1u << (e ? e : E_STATE));
+                }
                 bar_all();
                 continue;
             }
@@ -2520,7 +2703,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
             if (!is_ctrl()) {
                 long long ts = clock64();
                 const K *src = p.in + off;
-                if (n < k) {
+                if (ring) {
+                    // host memory that the next requests reuse: read it fresh
+                    for (uint32_t i = threadIdx.x; i < k; i += nmt())
+                        base[i] = i < n ? __ldcv(src + i) : kmax<K>();
+                } else if (n < k) {
                     for (uint32_t i = threadIdx.x; i < k; i += nmt())
                         base[i] = i < n ? __ldcg(src + i) : kmax<K>();
                 } else {
@@ -2550,6 +2737,14 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         // heaps go on (the failed heap's later ops are skipped)
         if (!ok && !multi) break;
         bar_all();
+        if (ring && threadIdx.x == 0) {
+            uint32_t st = 0;
+            if (!ok) {
+                const uint32_t e = ld_relaxed(&H.hdr->err);
+                st = 1u << (e ? e : E_STATE);
+            }
+            ring_complete(p, ring_req, st);
+        }
     }
     bar_all();
     if (threadIdx.x == 0) {

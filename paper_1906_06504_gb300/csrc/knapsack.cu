@@ -377,6 +377,11 @@ int collect(knapsack_t s, cudaStream_t st, unsigned long long *kept)
 
 extern "C" {
 
+gheap_t knapsack_heap(knapsack_t s)
+{
+    return s ? s->heap : nullptr;
+}
+
 int knapsack_destroy(knapsack_t s)
 {
     if (!s) return GHEAP_ERR_ARG;

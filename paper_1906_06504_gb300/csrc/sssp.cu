@@ -317,6 +317,11 @@ int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t
 
 extern "C" {
 
+gheap_t sssp_heap(sssp_t s)
+{
+    return s ? s->heap : nullptr;
+}
+
 int sssp_destroy(sssp_t s)
 {
     if (!s) return GHEAP_ERR_ARG;

@@ -57,6 +57,9 @@ def lib():
             "heap_set_launch": (ctypes.c_int, [vp, u32, u32]),
             "heap_set_timeout": (ctypes.c_int, [vp, u64]),
             "heap_set_yields": (ctypes.c_int, [vp, u32]),
+            "heap_set_stats": (ctypes.c_int, [vp, u32]),
+            "sssp_heap": (vp, [vp]),
+            "knapsack_heap": (vp, [vp]),
             "heap_insert": (ctypes.c_int, [vp, vp, u64, vp]),
             "heap_delete_min": (ctypes.c_int, [vp, vp, u64, vp, vp]),
             "heap_ops": (ctypes.c_int, [vp, vp, u64, vp, vp, vp, u64, vp]),
@@ -86,6 +89,15 @@ def lib():
             "heapset_graph_launch": (ctypes.c_int, [vp, vp]),
             "heapset_graph_destroy": (ctypes.c_int, [vp]),
             "heap_insert_dev": (ctypes.c_int, [vp, vp, vp, u64, vp]),
+            "heapring_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, u32, u64, u64, u64]),
+            "heapring_destroy": (ctypes.c_int, [vp]),
+            "heapring_attach": (ctypes.c_int, [vp, u32]),
+            "heapring_start": (ctypes.c_int, [vp]),
+            "heapring_stop": (ctypes.c_int, [vp]),
+            "heapring_submit": (ctypes.c_int, [vp, u32, vp, vp, vp, vp, vp]),
+            "heapring_poll": (ctypes.c_int, [vp, vp, vp, vp, u32, u32p]),
+            "heapring_take": (ctypes.c_int, [vp, u32, vp, vp, u64, vp]),
+            "heapring_pending": (ctypes.c_int, [vp, u64p]),
             "heap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             # gheap_apps.h
             "sssp_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64, u32, u32, u64]),
@@ -152,6 +164,10 @@ class GHeap:
 
     def set_timeout(self, ns):
         _check(lib().heap_set_timeout(self._h, int(ns)), "heap_set_timeout")
+
+    def set_stats(self, on):
+        """Device counters on or off for later launches (stats())."""
+        _check(lib().heap_set_stats(self._h, 1 if on else 0), "heap_set_stats")
 
     def set_yields(self, n):
         """Root hand-backs before a DEL marks an in-flight INS target (0 = the
@@ -395,6 +411,100 @@ class SetGraph:
         if getattr(self, "_g", None):
             lib().heapset_graph_destroy(self._g)
             self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GHeapRing:
+    """The serving ring of include/gheap.h over a GHeapSet: one persistent
+    launch takes insert/deleteMin requests from pinned host memory while the
+    host keeps submitting them (argument marshalling only)."""
+
+    def __init__(self, hset, max_requests=4096, max_ops=1 << 15, in_keys=1 << 24,
+                 out_keys=1 << 24):
+        r = ctypes.c_void_p()
+        _check(lib().heapring_create(ctypes.byref(r), hset._s, int(max_requests), int(max_ops),
+                                     int(in_keys), int(out_keys)), "heapring_create")
+        self._r = r
+        self.set = hset
+        self.key_dtype = np.uint32 if hset.key_bytes == 4 else np.uint64
+        self.max_requests = int(max_requests)
+        self.in_keys = int(in_keys)
+        self.out_keys = int(out_keys)
+        self._ids = np.zeros(self.max_requests, dtype=np.uint64)
+        self._cnt = np.zeros(self.max_requests, dtype=np.uint64)
+        self._st = np.zeros(self.max_requests, dtype=np.int32)
+        self.running = False
+
+    def start(self):
+        _check(lib().heapring_start(self._r), "heapring_start")
+        self.running = True
+
+    def stop(self):
+        self.running = False
+        _check(lib().heapring_stop(self._r), "heapring_stop")
+
+    def attach(self, i):
+        _check(lib().heapring_attach(self._r, int(i)), "heapring_attach")
+
+    def submit(self, heaps, kinds, sizes, keys=None):
+        """Appends requests (uint32 heaps, uint32 kinds OP_INS/OP_DEL, uint64
+        sizes; keys: the inserts' keys back to back).  Returns the ids of the
+        requests accepted, a prefix of the ones given."""
+        heaps = np.ascontiguousarray(heaps, dtype=np.uint32)
+        kinds = np.ascontiguousarray(kinds, dtype=np.uint32)
+        sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+        ids = np.zeros(heaps.size, dtype=np.uint64)
+        kp = None
+        if keys is not None and len(keys):
+            keys = np.ascontiguousarray(keys, dtype=self.key_dtype)
+            kp = ctypes.c_void_p(keys.ctypes.data)
+        rc = lib().heapring_submit(self._r, heaps.size, ctypes.c_void_p(heaps.ctypes.data),
+                                   ctypes.c_void_p(kinds.ctypes.data),
+                                   ctypes.c_void_p(sizes.ctypes.data), kp,
+                                   ctypes.c_void_p(ids.ctypes.data))
+        if rc < 0:
+            raise GHeapError(rc, "heapring_submit")
+        return ids[:rc]
+
+    def poll(self):
+        """(ids, counts, status) of the requests completed since the last poll."""
+        n = ctypes.c_uint32()
+        _check(lib().heapring_poll(self._r, ctypes.c_void_p(self._ids.ctypes.data),
+                                   ctypes.c_void_p(self._cnt.ctypes.data),
+                                   ctypes.c_void_p(self._st.ctypes.data), self.max_requests,
+                                   ctypes.byref(n)), "heapring_poll")
+        c = int(n.value)
+        return self._ids[:c].copy(), self._cnt[:c].copy(), self._st[:c].copy()
+
+    def take(self, ids, counts):
+        """Takes completed requests `ids` (with the counts poll reported):
+        returns one array per request (its deleteMin keys; empty for an
+        insert), views into one buffer, and frees the requests."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        counts = np.asarray(counts, dtype=np.uint64)
+        total = int(counts.sum())
+        out = np.empty(total, dtype=self.key_dtype)
+        got = np.zeros(ids.size, dtype=np.uint64)
+        _check(lib().heapring_take(self._r, ids.size, ctypes.c_void_p(ids.ctypes.data),
+                                   ctypes.c_void_p(out.ctypes.data), total,
+                                   ctypes.c_void_p(got.ctypes.data)), "heapring_take")
+        return np.split(out, np.cumsum(got)[:-1].astype(np.int64))
+
+    def pending(self):
+        v = ctypes.c_uint64()
+        _check(lib().heapring_pending(self._r, ctypes.byref(v)), "heapring_pending")
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "_r", None):
+            lib().heapring_destroy(self._r)
+            self._r = None
+            self.running = False
 
     def __del__(self):
         try:

@@ -1,34 +1,45 @@
-"""Continuously batched serving of insert / deleteMin requests over many heaps.
+"""Continuous batching of insert / deleteMin requests over many heaps.
 
 Requests name a heap and carry either keys to insert or a count of smallest
-keys to remove.  They arrive over time; the server keeps every heap resident
-on the device and, whenever the GPU can take more work, forms a batch of the
-requests that have arrived -- at most one per heap, taken in arrival order, so
-that each heap sees its requests in FIFO order -- and launches the whole batch
-as one heap-set launch (include/gheap.h heapset_ops_req): requests on
-different heaps run concurrently on the device, and up to `depth` batches are
-queued on the stream while the host forms the next one.  A heap is admitted
-(allocated and bound into the set) on its first request when the HBM budget
-allows; a heap that is empty and idle is evicted when the budget is needed.
+keys to remove.  They arrive over time.  The server keeps every heap resident
+on the device in one heap set and serves them through the set's serving ring
+(include/gheap.h heapring_*): one persistent launch runs for the whole
+session, and each request that has arrived is appended to the ring as soon as
+its heap may take it, so it starts on the device while earlier requests are
+still running there -- requests on different heaps run side by side, and
+requests on one heap run in their arrival order, several at a time.  The
+launch reads the requests and keys from pinned host memory and writes the
+results and completion records back there; the host loop only submits, polls
+and collects.  A heap is admitted (allocated and bound into the set) on its
+first request when the HBM budget allows, evicting heaps that are empty and
+idle when the budget is needed (the launch is paused for that).
+
+Requests a heap cannot hold are refused with an error rather than lost: an
+insert that could take a heap past its capacity waits while earlier requests
+of that heap are in flight (their deleteMins may make room) and is refused as
+full when none are; one larger than the whole capacity, or larger than the
+ring's key arenas, is refused at once.
 
 All heap arithmetic runs in the CUDA kernels behind the C ABI; this module
-only arranges requests into operation lists, moves keys between pinned host
-buffers and the device, and keeps time.
+only arranges requests, copies keys into and out of the ring, and keeps time.
 """
 import collections
 import time
 
 import numpy as np
 
-from .heap import GHeap, GHeapSet, OP_DEL, OP_INS, SET_CURSOR, SETOP_DTYPE
+from .heap import GHeap, GHeapRing, GHeapSet, GHeapError, OP_DEL, OP_INS
 
 
 class Request:
     """One client request.  kind "ins" carries `keys`; kind "del" asks for the
     `n` smallest keys.  After serving: `result` (del: the keys removed,
-    ascending), `t_done` (seconds since the run started) and `latency`."""
+    ascending), `t_submit` and `t_done` (seconds since the run started, when
+    it entered the ring and when its completion was seen), `latency` (from
+    arrival) and `error` (None, or why it was refused or failed)."""
 
-    __slots__ = ("rid", "arrival", "heap", "kind", "keys", "n", "result", "t_done", "latency")
+    __slots__ = ("rid", "arrival", "heap", "kind", "keys", "n", "result", "t_done", "latency",
+                 "t_submit", "error")
 
     def __init__(self, rid, arrival, heap, kind, keys=None, n=0):
         self.rid = rid
@@ -40,30 +51,16 @@ class Request:
         self.result = None
         self.t_done = None
         self.latency = None
-
-
-class _Slot:
-    """Pinned host and device buffers of one in-flight batch."""
-
-    def __init__(self, torch, max_ops, max_keys, max_reqs, key_dtype):
-        pin = dict(pin_memory=True)
-        self.h_ops = torch.empty(max_ops * SETOP_DTYPE.itemsize, dtype=torch.uint8, **pin)
-        self.h_in = torch.empty(max_keys, dtype=key_dtype, **pin)
-        self.h_out = torch.empty(max_keys, dtype=key_dtype, **pin)
-        self.h_base = torch.empty(max_reqs, dtype=torch.int64, **pin)
-        self.h_cur = torch.empty(max_reqs, dtype=torch.int64, **pin)
-        self.d_ops = torch.empty(max_ops * SETOP_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-        self.d_in = torch.empty(max_keys, dtype=key_dtype, device="cuda")
-        self.d_out = torch.empty(max_keys, dtype=key_dtype, device="cuda")
-        self.d_base = torch.empty(max_reqs, dtype=torch.int64, device="cuda")
-        self.d_cur = torch.empty(max_reqs, dtype=torch.int64, device="cuda")
-        self.event = torch.cuda.Event()
-        self.batch = None
+        self.t_submit = None
+        self.error = None         # why the request was refused or failed, else None
 
 
 class HeapServer:
-    def __init__(self, capacities, k=1024, key_bytes=4, hbm_budget=None, depth=2,
-                 max_batch_keys=1 << 22, max_batch_reqs=4096, items_per_thread=None, ctas=0):
+    """Serves requests on `capacities` heaps (keys each) of node capacity k."""
+
+    def __init__(self, capacities, k=1024, key_bytes=4, hbm_budget=None, max_inflight=8192,
+                 max_ops=1 << 16, arena_keys=1 << 24, items_per_thread=None, ctas=0,
+                 stats=False):
         import torch
         self.torch = torch
         self.k = int(k)
@@ -72,21 +69,18 @@ class HeapServer:
         self.n_heaps = len(self.capacities)
         self.budget = hbm_budget if hbm_budget is not None else 1 << 62
         self.used = 0
-        self.set = GHeapSet([0] * self.n_heaps, k=k, key_bytes=key_bytes)
+        self.set = GHeapSet([0] * self.n_heaps, k=k, key_bytes=key_bytes, stats=stats)
         if items_per_thread is not None or ctas:
             self.set.set_launch(ctas=ctas, items_per_thread=items_per_thread or 8)
+        self.ring = GHeapRing(self.set, max_requests=max_inflight, max_ops=max_ops,
+                              in_keys=arena_keys, out_keys=arena_keys)
         self.heaps = [None] * self.n_heaps       # owning GHeap per admitted heap
-        self.size = [0] * self.n_heaps           # keys held (host view)
-        self.busy = [0] * self.n_heaps           # requests in flight
-        key_dtype = torch.int32 if key_bytes == 4 else torch.int64
+        self.size = [0] * self.n_heaps           # keys held: an upper bound
+        self.busy = [0] * self.n_heaps           # requests in the ring
         self.np_key = np.uint32 if key_bytes == 4 else np.uint64
-        max_ops = max_batch_reqs + max_batch_keys // k + 1
-        self.max_keys = max_batch_keys
-        self.max_reqs = max_batch_reqs
-        self.slots = [_Slot(torch, max_ops, max_batch_keys, max_batch_reqs, key_dtype)
-                      for _ in range(depth)]
-        self.stream = torch.cuda.current_stream()
-        self.stats = {"batches": 0, "admitted": 0, "evicted": 0, "ops": 0}
+        self.stream = torch.cuda.Stream()
+        self.stats = {"submits": 0, "admitted": 0, "evicted": 0, "requests": 0,
+                      "max_inflight": 0, "submitted_while_busy": 0, "refused": 0}
 
     # -- heap admission under the HBM budget
     def _bytes(self, h):
@@ -97,26 +91,40 @@ class HeapServer:
         if self.heaps[h] is not None:
             return True
         need = self._bytes(h)
-        if self.used + need > self.budget:
-            # evict empty, idle heaps that nobody is waiting for
-            for g in range(self.n_heaps):
-                if self.used + need <= self.budget:
-                    break
-                if (self.heaps[g] is not None and self.size[g] == 0 and self.busy[g] == 0
-                        and g not in pending_heaps):
-                    self.set.unbind(g, stream=self.stream)
-                    self.heaps[g].close()
-                    self.heaps[g] = None
-                    self.used -= self._bytes(g)
-                    self.stats["evicted"] += 1
+        if need > self.budget:
+            return False
+        was_running = self.ring.running
+        if was_running:
+            # heap memory is allocated and freed with the launch paused
+            self.ring.stop()
+        try:
+            if self.used + need > self.budget:
+                # evict empty, idle heaps that nobody is waiting for
+                for g in range(self.n_heaps):
+                    if self.used + need <= self.budget:
+                        break
+                    if (self.heaps[g] is not None and self.size[g] == 0 and self.busy[g] == 0
+                            and g not in pending_heaps):
+                        code = self.heaps[g].sync_code()
+                        if code != 0:
+                            raise GHeapError(code, "heap %d before eviction" % g)
+                        self.set.unbind(g, stream=self.stream)
+                        self.heaps[g].close()
+                        self.heaps[g] = None
+                        self.used -= self._bytes(g)
+                        self.stats["evicted"] += 1
             if self.used + need > self.budget:
                 return False
-        heap = GHeap(self.capacities[h], k=self.k, key_bytes=self.key_bytes)
-        self.set.bind(h, heap, stream=self.stream)
-        self.heaps[h] = heap
-        self.used += need
-        self.stats["admitted"] += 1
-        return True
+            heap = GHeap(self.capacities[h], k=self.k, key_bytes=self.key_bytes)
+            self.set.bind(h, heap, stream=self.stream)
+            self.ring.attach(h)
+            self.heaps[h] = heap
+            self.used += need
+            self.stats["admitted"] += 1
+            return True
+        finally:
+            if was_running:
+                self.ring.start()
 
     def preadmit(self, heaps):
         """Admits heaps ahead of their first request (allocation is not free)."""
@@ -125,135 +133,145 @@ class HeapServer:
                 raise RuntimeError("heap %d does not fit the HBM budget" % h)
         self.torch.cuda.synchronize()
 
-    # -- one batch
-    def _select(self, pending):
-        """At most one request per heap, in arrival order; a heap's later
-        requests wait behind its earlier ones."""
+    # -- checks that do not depend on the heap's state
+    def _refuse_reason(self, r):
+        if r.n < 1:
+            return "empty request"
+        if r.kind == "ins" and r.n > self.capacities[r.heap]:
+            return "insert of %d keys exceeds the heap's capacity %d" % (
+                r.n, self.capacities[r.heap])
+        if r.n > min(self.ring.in_keys, self.ring.out_keys):
+            return "request of %d keys exceeds the ring's key arenas (%d)" % (
+                r.n, min(self.ring.in_keys, self.ring.out_keys))
+        if self._bytes(r.heap) > self.budget:
+            return "heap %d alone exceeds the HBM budget" % r.heap
+        return None
+
+    def _select(self, pending, now):
+        """The requests to submit now: per heap in arrival order, each heap
+        stopping at its first request that must wait (an insert that could
+        overflow the heap, or a heap that cannot be admitted yet)."""
         taken, blocked, keep = [], set(), collections.deque()
-        keys_in = keys_out = 0
+        taken_heaps = set()
         pend_heaps = {r.heap for r in pending}
         while pending:
             r = pending.popleft()
             h = r.heap
-            if r.kind == "ins":
-                fits = keys_in + r.n <= self.max_keys
-            else:
-                fits = keys_out + min(r.n, self.size_hint(h)) <= self.max_keys
-            if (h in blocked or len(taken) >= self.max_reqs or not fits
-                    or not self._admit(h, pend_heaps)):
+            if h in blocked:
+                keep.append(r)
+                continue
+            why = self._refuse_reason(r)
+            if why is not None:
+                r.error = why
+                r.t_done = now
+                r.latency = now - r.arrival
+                self.stats["refused"] += 1
+                continue
+            fits = r.kind == "del" or self.size[h] + r.n <= self.capacities[h]
+            if not fits and self.busy[h] == 0 and h not in taken_heaps:
+                # nothing of this heap is in flight that could make room, and
+                # its later requests must not overtake this one: refuse it
+                r.error = "heap %d full: %d keys held, insert of %d, capacity %d" % (
+                    h, self.size[h], r.n, self.capacities[h])
+                r.t_done = now
+                r.latency = now - r.arrival
+                self.stats["refused"] += 1
+                continue
+            if not fits or not self._admit(h, pend_heaps):
                 blocked.add(h)
                 keep.append(r)
                 continue
-            blocked.add(h)
             taken.append(r)
+            taken_heaps.add(h)
             if r.kind == "ins":
-                keys_in += r.n
-            else:
-                keys_out += min(r.n, self.size_hint(h))
+                self.size[h] += r.n
         pending.extend(keep)
         return taken
 
-    def size_hint(self, h):
-        # keys inserted (in flight included) minus keys whose removal has been
-        # reported: an upper bound on what a deleteMin can return
-        return max(self.size[h], 0)
-
-    def _launch(self, slot, batch):
-        torch = self.torch
-        k = self.k
-        ops = []
-        in_parts = []
-        in_off = 0
-        out_off = 0
-        bases = np.zeros(len(batch), dtype=np.int64)
-        for ri, r in enumerate(batch):
-            if r.kind == "ins":
-                n = r.n
-                for j in range(0, n, k):
-                    ops.append((r.heap, (OP_INS << 24) | min(k, n - j), in_off + j))
-                in_parts.append(np.asarray(r.keys, dtype=self.np_key))
-                in_off += n
-                self.size[r.heap] += n
-            else:
-                want = min(r.n, self.size_hint(r.heap))
-                bases[ri] = out_off
-                for j in range(0, want, k):
-                    ops.append((r.heap, (OP_DEL << 24) | SET_CURSOR | min(k, want - j), ri))
-                out_off += want
+    def _submit(self, batch, now, inflight):
+        if not batch:
+            return 0
+        heaps = np.array([r.heap for r in batch], dtype=np.uint32)
+        kinds = np.array([OP_INS if r.kind == "ins" else OP_DEL for r in batch], dtype=np.uint32)
+        sizes = np.array([r.n for r in batch], dtype=np.uint64)
+        ins = [np.asarray(r.keys, dtype=self.np_key) for r in batch if r.kind == "ins"]
+        keys = np.concatenate(ins) if ins else None
+        ids = self.ring.submit(heaps, kinds, sizes, keys)
+        busy_before = len(inflight)
+        for r, rid in zip(batch[:ids.size], ids):
+            inflight[int(rid)] = r
+            r.t_submit = now
             self.busy[r.heap] += 1
-        ops = np.array(ops, dtype=SETOP_DTYPE)
-        nb = ops.size * SETOP_DTYPE.itemsize
-        slot.h_ops[:nb].numpy()[:] = ops.view(np.uint8)
-        if in_off:
-            slot.h_in[:in_off].numpy()[:] = np.concatenate(in_parts).view(
-                np.int32 if self.key_bytes == 4 else np.int64)
-        slot.h_base[:len(batch)].numpy()[:] = bases
-        s = self.stream
-        slot.d_ops[:nb].copy_(slot.h_ops[:nb], non_blocking=True)
-        if in_off:
-            slot.d_in[:in_off].copy_(slot.h_in[:in_off], non_blocking=True)
-        slot.d_base[:len(batch)].copy_(slot.h_base[:len(batch)], non_blocking=True)
-        slot.d_cur[:len(batch)].zero_()
-        if ops.size:
-            self.set.ops_req(slot.d_ops[:nb], slot.d_in if in_off else None, slot.d_out, None,
-                             slot.d_base, slot.d_cur, stream=s)
-        if out_off:
-            slot.h_out[:out_off].copy_(slot.d_out[:out_off], non_blocking=True)
-        slot.h_cur[:len(batch)].copy_(slot.d_cur[:len(batch)], non_blocking=True)
-        slot.event.record(s)
-        slot.batch = (batch, bases)
-        self.stats["batches"] += 1
-        self.stats["ops"] += int(ops.size)
+        if ids.size and busy_before:
+            self.stats["submitted_while_busy"] += int(ids.size)
+        self.stats["submits"] += 1
+        self.stats["max_inflight"] = max(self.stats["max_inflight"], len(inflight))
+        return int(ids.size)
 
-    def _finish(self, slot, now):
-        batch, bases = slot.batch
-        got = slot.h_cur[:len(batch)].numpy()
-        out = slot.h_out.numpy().view(self.np_key)
-        for ri, r in enumerate(batch):
+    def _collect(self, inflight, t0):
+        ids, counts, status = self.ring.poll()
+        if ids.size == 0:
+            return 0
+        now = time.perf_counter() - t0
+        # inserts report their size as the count; only deleteMins return keys
+        dels = np.array([inflight[i].kind == "del" for i in ids.tolist()], dtype=bool)
+        outs = self.ring.take(ids, np.where(dels, counts, 0))
+        for rid, st, out in zip(ids.tolist(), status.tolist(), outs):
+            r = inflight.pop(rid)
             self.busy[r.heap] -= 1
             if r.kind == "del":
-                c = int(got[ri])
-                r.result = out[bases[ri]:bases[ri] + c].copy()
-                self.size[r.heap] -= c
+                r.result = out
+                self.size[r.heap] -= out.size
+            if st != 0:
+                r.error = "device error %d on heap %d" % (st, r.heap)
             r.t_done = now
             r.latency = now - r.arrival
-        slot.batch = None
+        self.stats["requests"] += int(ids.size)
+        return int(ids.size)
 
     def run(self, requests, realtime=True):
         """Serves `requests` (arrival times in seconds from the start).  With
         realtime=False every request is treated as already arrived."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
         pending = collections.deque()
+        inflight = {}
         nxt = 0
-        free = list(self.slots)
-        busy = collections.deque()
+        self.ring.start()
         t0 = time.perf_counter()
-        while nxt < len(reqs) or pending or busy:
-            now = time.perf_counter() - t0
-            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
-                pending.append(reqs[nxt])
-                nxt += 1
-            while busy and busy[0].event.query():
-                slot = busy.popleft()
-                self._finish(slot, time.perf_counter() - t0)
-                free.append(slot)
-            if free and pending:
-                batch = self._select(pending)
-                if batch:
-                    slot = free.pop()
-                    self._launch(slot, batch)
-                    busy.append(slot)
+        try:
+            while nxt < len(reqs) or pending or inflight:
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
+                    pending.append(reqs[nxt])
+                    nxt += 1
+                progressed = self._collect(inflight, t0)
+                if pending:
+                    batch = self._select(pending, now)
+                    done = self._submit(batch, now, inflight)
+                    for r in reversed(batch[done:]):
+                        # the ring was full: these wait at the front, in order
+                        if r.kind == "ins":
+                            self.size[r.heap] -= r.n
+                        pending.appendleft(r)
+                    progressed += done
+                if progressed:
                     continue
-            if busy:
-                continue      # poll the oldest batch
-            if nxt < len(reqs) and not pending:
-                time.sleep(max(0.0, min(reqs[nxt].arrival - now, 1e-3)))
-            elif pending and not busy:
-                raise RuntimeError("pending requests cannot be admitted within the HBM budget")
-        self.set.sync()
+                if pending and not inflight:
+                    raise RuntimeError("pending requests cannot be admitted within the HBM "
+                                       "budget (no heap is empty and idle)")
+                if not inflight and nxt < len(reqs):
+                    time.sleep(max(0.0, min(reqs[nxt].arrival - now, 1e-3)))
+        finally:
+            self.ring.stop()
+        code = self.set.sync_code()
+        if code != 0:
+            raise GHeapError(code, "heap set after serving")
         return reqs
 
     def close(self):
+        if self.ring is not None:
+            self.ring.close()
+            self.ring = None
         for h in range(self.n_heaps):
             if self.heaps[h] is not None:
                 self.set.unbind(h, stream=self.stream)
@@ -263,8 +281,11 @@ class HeapServer:
 
 
 def latency_summary(reqs):
-    lat = np.array([r.latency for r in reqs if r.latency is not None])
-    keys = sum(r.n if r.kind == "ins" else (0 if r.result is None else r.result.size) for r in reqs)
+    """p50/p99 latency (arrival to completion seen) of the served requests and
+    the keys they moved per second of the run."""
+    ok = [r for r in reqs if r.latency is not None and r.error is None]
+    lat = np.array([r.latency for r in ok])
+    keys = sum(r.n if r.kind == "ins" else (0 if r.result is None else r.result.size) for r in ok)
     span = max(r.t_done for r in reqs) - min(r.arrival for r in reqs)
     return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "keys": int(keys),

@@ -1,11 +1,14 @@
 """Host-side policy of the serving loop on CPU, with the device side faked.
 
-The server forms each batch from the arrived requests -- at most one per
-heap, in arrival order, so that every heap sees its requests in FIFO order --
-within a request and key budget, and admits a heap on its first request when
-the HBM budget allows, evicting heaps that are empty, idle and not waited
-for.  These rules decide which requests share a launch; they involve no heap
-arithmetic, so they are checked here against a fake heap set.
+The server submits arrived requests to the serving ring as soon as their heap
+may take them: per heap in arrival order (so every heap sees its requests in
+FIFO order, several in flight at once), holding an insert that could take its
+heap past capacity until deleteMins make room, refusing requests no heap or
+ring could ever hold, and admitting a heap on its first request when the HBM
+budget allows, evicting heaps that are empty, idle and not waited for (with
+the ring's launch paused meanwhile).  These rules decide what enters the ring
+and when; they involve no heap arithmetic, so they are checked here against
+fakes of the heap, the heap set and the ring.
 """
 import collections
 
@@ -18,9 +21,13 @@ from paper_1906_06504_gb300.serve import HeapServer, Request
 
 class FakeHeap:
     closed = 0
+    code = 0
 
     def __init__(self, capacity, k=1024, key_bytes=4):
         self.capacity = capacity
+
+    def sync_code(self):
+        return FakeHeap.code
 
     def close(self):
         FakeHeap.closed += 1
@@ -38,8 +45,27 @@ class FakeSet:
         del self.bound[i]
 
 
-def make_server(capacities, k=4, budget=None, max_keys=64, max_reqs=8):
-    """A HeapServer without device buffers: only its host policy is used."""
+class FakeRing:
+    def __init__(self, keys=1 << 20):
+        self.in_keys = self.out_keys = keys
+        self.running = False
+        self.log = []
+
+    def start(self):
+        self.running = True
+        self.log.append("start")
+
+    def stop(self):
+        self.running = False
+        self.log.append("stop")
+
+    def attach(self, i):
+        assert not self.running
+        self.log.append("attach %d" % i)
+
+
+def make_server(capacities, k=4, budget=None, arena=1 << 20):
+    """A HeapServer without device state: only its host policy is used."""
     s = HeapServer.__new__(HeapServer)
     s.k = k
     s.key_bytes = 4
@@ -48,13 +74,13 @@ def make_server(capacities, k=4, budget=None, max_keys=64, max_reqs=8):
     s.budget = budget if budget is not None else 1 << 62
     s.used = 0
     s.set = FakeSet()
+    s.ring = FakeRing(arena)
     s.heaps = [None] * s.n_heaps
     s.size = [0] * s.n_heaps
     s.busy = [0] * s.n_heaps
-    s.max_keys = max_keys
-    s.max_reqs = max_reqs
     s.stream = None
-    s.stats = {"batches": 0, "admitted": 0, "evicted": 0, "ops": 0}
+    s.stats = {"submits": 0, "admitted": 0, "evicted": 0, "requests": 0, "max_inflight": 0,
+               "submitted_while_busy": 0, "refused": 0}
     return s
 
 
@@ -62,6 +88,7 @@ def make_server(capacities, k=4, budget=None, max_keys=64, max_reqs=8):
 def fake_heap(monkeypatch):
     monkeypatch.setattr(serve, "GHeap", FakeHeap)
     FakeHeap.closed = 0
+    FakeHeap.code = 0
 
 
 def ins(rid, heap, n):
@@ -72,36 +99,47 @@ def dele(rid, heap, n):
     return Request(rid, 0.0, heap, "del", n=n)
 
 
-def test_one_request_per_heap_fifo():
+def test_several_requests_per_heap_in_arrival_order():
     s = make_server([100] * 3)
     pending = collections.deque([ins(0, 0, 4), ins(1, 0, 4), ins(2, 1, 4), dele(3, 0, 2),
                                  ins(4, 2, 4), ins(5, 1, 4)])
-    first = s._select(pending)
-    assert [r.rid for r in first] == [0, 2, 4]
-    # the rest keep their order; heap 0's requests stay in arrival order
-    assert [r.rid for r in pending] == [1, 3, 5]
-    second = s._select(pending)
-    assert [r.rid for r in second] == [1, 5]
-    assert [r.rid for r in pending] == [3]
+    got = s._select(pending, 0.0)
+    assert [r.rid for r in got] == [0, 1, 2, 3, 4, 5]
+    assert not pending
+    assert s.size == [8, 8, 4]
 
 
-def test_request_and_key_budgets():
-    s = make_server([1000] * 6, max_keys=10, max_reqs=2)
-    pending = collections.deque([ins(0, 0, 6), ins(1, 1, 6), ins(2, 2, 3), ins(3, 3, 1)])
-    got = s._select(pending)
-    # request 1 would pass the key budget (12 > 10); requests are capped at 2
-    assert [r.rid for r in got] == [0, 2]
-    assert [r.rid for r in pending] == [1, 3]
+def test_insert_waits_for_room_and_blocks_only_its_heap():
+    s = make_server([10, 10])
+    s._admit(0, set())
+    s._admit(1, set())
+    s.size = [8, 0]
+    s.busy = [1, 0]           # an earlier request of heap 0 is in flight
+    pending = collections.deque([ins(0, 0, 4), dele(1, 0, 3), ins(2, 1, 4), ins(3, 0, 1)])
+    got = s._select(pending, 0.0)
+    # heap 0's insert could overflow it: it and everything after it on heap 0
+    # wait, in order; heap 1 goes on
+    assert [r.rid for r in got] == [2]
+    assert [r.rid for r in pending] == [0, 1, 3]
+    # the deleteMins of heap 0 made room
+    s.size[0] = 5
+    got = s._select(pending, 0.0)
+    assert [r.rid for r in got] == [0, 1, 3]
 
 
-def test_delete_counts_what_the_heap_can_return():
-    s = make_server([1000] * 2, max_keys=8)
-    s.size = [3, 100]
-    pending = collections.deque([dele(0, 0, 50), dele(1, 1, 5), dele(2, 1, 1)])
-    got = s._select(pending)
-    # heap 0 can return 3 keys, heap 1 five: 8 keys fit; request 2 waits (FIFO)
-    assert [r.rid for r in got] == [0, 1]
-    assert [r.rid for r in pending] == [2]
+def test_refusal_reasons():
+    s = make_server([10, 1 << 30], arena=64)
+    s.budget = s._bytes(0) + 1
+    reqs = [ins(0, 0, 11), dele(1, 0, 65), ins(2, 1, 4), ins(3, 0, 10)]
+    assert "capacity" in s._refuse_reason(reqs[0])
+    assert "arenas" in s._refuse_reason(reqs[1])
+    assert "HBM budget" in s._refuse_reason(reqs[2])
+    assert s._refuse_reason(reqs[3]) is None
+    pending = collections.deque(reqs)
+    got = s._select(pending, 0.25)
+    assert [r.rid for r in got] == [3]
+    for r in reqs[:3]:
+        assert r.error and r.t_done == 0.25 and r.result is None
 
 
 def test_admission_evicts_empty_idle_heaps_only():
@@ -127,14 +165,58 @@ def test_admission_evicts_empty_idle_heaps_only():
     assert set(s.set.bound) == {0, 2}
 
 
+def test_admission_pauses_a_running_ring():
+    s = make_server([400] * 2)
+    s.ring.start()
+    assert s._admit(1, set())
+    assert s.ring.log == ["start", "stop", "attach 1", "start"]
+    assert s.ring.running
+    # an admitted heap needs no pause
+    assert s._admit(1, set())
+    assert s.ring.log[-1] == "start" and len(s.ring.log) == 4
+
+
+def test_eviction_reports_a_heap_error():
+    s = make_server([400] * 2)
+    s.budget = s._bytes(0)
+    assert s._admit(0, set())
+    FakeHeap.code = -4
+    from paper_1906_06504_gb300.heap import GHeapError
+    with pytest.raises(GHeapError):
+        s._admit(1, set())
+
+
 def test_admission_failure_keeps_the_request_pending():
     s = make_server([400] * 2)
     s.budget = s._bytes(0)
     assert s._admit(0, set())
     s.size[0] = 1
     pending = collections.deque([ins(0, 1, 4), ins(1, 0, 4)])
-    got = s._select(pending)
+    got = s._select(pending, 0.0)
     # heap 1 cannot be admitted (heap 0 is not empty): its request waits,
     # heap 0's request is served
     assert [r.rid for r in got] == [1]
     assert [r.rid for r in pending] == [0]
+
+
+def test_insert_that_cannot_fit_is_refused_when_its_heap_is_idle():
+    s = make_server([10, 10])
+    s._admit(0, set())
+    s.size = [8, 0]
+    pending = collections.deque([ins(0, 0, 4), dele(1, 0, 3)])
+    got = s._select(pending, 0.5)
+    # nothing of heap 0 is in flight: waiting cannot help, and the deleteMin
+    # behind the insert must not overtake it -- the insert is refused as full
+    assert [r.rid for r in got] == [1]
+    assert not pending and s.stats["refused"] == 1
+
+
+def test_insert_waits_for_a_deletemin_submitted_with_it():
+    s = make_server([10])
+    s._admit(0, set())
+    s.size = [8]
+    pending = collections.deque([dele(0, 0, 5), ins(1, 0, 4)])
+    got = s._select(pending, 0.0)
+    # the deleteMin ahead of it may make room: the insert waits, not refused
+    assert [r.rid for r in got] == [0]
+    assert [r.rid for r in pending] == [1] and s.stats["refused"] == 0
