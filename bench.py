@@ -426,13 +426,16 @@ def run_mixed(torch, n_prefill=1 << 24, n_pairs=1 << 16, k=K, ipt=8, ctas=0, see
 
 
 def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_up=False,
-                best=None):
+                best=None, scale=1.0, cpu=True):
     """Batched heaps: 256 heaps with log-uniform sizes 2^10 to 2^22 keys; one
     launch inserts all of them, one launch deletes all, both replayed from
-    captured CUDA graphs; k and the merge width autotuned (or `best`)."""
+    captured CUDA graphs; k and the merge width autotuned (or `best`).
+    `scale` shrinks every heap (a small case for profiling)."""
     from paper_1906_06504_gb300 import inputs, tune as tuner
     from paper_1906_06504_gb300.heap import GHeapSet, OP_INS, OP_DEL
     sizes = inputs.loguniform_sizes(inputs.config_seed(5), n_heaps, 10, 22)
+    if scale != 1.0:
+        sizes = np.maximum(1, (sizes * scale).astype(np.int64))
     total = int(sizes.sum())
     keys = inputs.keys_u32(inputs.config_seed(5), total)
     if best is not None:
@@ -483,7 +486,7 @@ def run_batched(torch, steps=3, tune=True, n_heaps=256, verify_heaps=8, bottom_u
         torch.cuda.synchronize()
         st = hs.stats()
     step_bytes = node_bytes(st, k, 4) + 2 * total * 4
-    cpu_v, cores, cpu_s = cpu_oracle_heapset(sizes, keys)
+    cpu_v, cores, cpu_s = cpu_oracle_heapset(sizes, keys) if cpu else (None, None, None)
     return {"workload": "256 heaps, log-uniform 2^10..2^22 keys (%d total), insert-all + "
                         "deleteMin-all, one launch each, CUDA-graph replay" % total,
             "insert": "bottom-up" if bottom_up else "top-down",
@@ -779,10 +782,12 @@ def sweep_levels(torch, k=1024, ipt=8, pairs=1 << 14):
     `pairs` ins-del pairs of k keys from all blocks."""
     for L in (6, 8, 10, 12, 14, 16, 18):
         pre = ((1 << L) - 1) * k
+        # the oracle replays the runs up to a 2^24-key prefill (a bigger one
+        # takes minutes to replay on one host core)
         r = run_mixed(torch, n_prefill=pre, n_pairs=pairs, k=k, ipt=ipt, seed_off=L,
-                      count=False)
+                      count=False, replay=pre <= (1 << 24))
         yield {"sweep": "levels", "levels": L, "prefill_keys": pre, "pairs": pairs,
-               "ms": r["ms"], "keys_per_s": r["value"]}
+               "ms": r["ms"], "keys_per_s": r["value"], "exact": r.get("exact")}
 
 
 def sweep_serve(torch, n_requests=20000):
@@ -809,7 +814,17 @@ def sweep_heapset(torch):
     yield dict(sweep="heapset", **r)
 
 
-SWEEPS = {"apps": sweep_apps, "heapset": sweep_heapset, "k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
+def sweep_heapset_small(torch):
+    """The heap-set workload with every heap at 1/8 of its size (about 15 M
+    keys; inputs, outputs and heaps each still larger than L2): a small case
+    of the same launches for multi-pass profiler captures."""
+    r = run_batched(torch, steps=3, best={"k": 2048, "items_per_thread": 16}, scale=0.125,
+                    cpu=False)
+    r.pop("autotune", None)
+    yield dict(sweep="heapset_small", **r)
+
+
+SWEEPS = {"apps": sweep_apps, "heapset": sweep_heapset, "heapset_small": sweep_heapset_small, "k_threads": sweep_k_threads, "ctas": sweep_ctas, "distribution": sweep_distribution,
           "partial": sweep_partial, "levels": sweep_levels, "serve_rate": sweep_serve}
 
 
