@@ -533,7 +533,8 @@ def run_serve(torch, n_requests=20000, rate=50000.0, n_heaps=256, count=True):
                  "submitted_while_busy": info["submitted_while_busy"],
                  "refused": info["refused"],
                  "workload": "Poisson arrivals, 1..4096 keys, 50/50 insert/deleteMin, "
-                             "256 heaps, k=1024, one persistent serving launch"})
+                             "256 heaps, k=1024, one persistent serving launch, native host "
+                             "loop"})
     if count:
         _, cinfo = serve(True, False)
         span_s = summ["keys"] / summ["keys_per_s"]
@@ -792,8 +793,10 @@ def sweep_levels(torch, k=1024, ipt=8, pairs=1 << 14):
 
 def sweep_serve(torch, n_requests=20000):
     """Serving: arrival rate swept up to saturation; p50/p99 latency."""
-    for rate in (10000.0, 50000.0, 100000.0, 200000.0, 300000.0, 400000.0, 800000.0):
-        r = run_serve(torch, n_requests=n_requests, rate=rate, count=False)
+    for rate in (10000.0, 50000.0, 100000.0, 200000.0, 400000.0, 800000.0, 1200000.0,
+                 1600000.0):
+        r = run_serve(torch, n_requests=n_requests if rate < 1e6 else 2 * n_requests, rate=rate,
+                      count=False)
         r["sweep"] = "serve_rate"
         yield r
 
@@ -955,7 +958,7 @@ def run_gpu(args):
         extras["mixed"] = run_mixed(torch, ipt=args.ipt)
         extras["batched"] = run_batched(torch, tune=not args.no_tune)
         extras["serve"] = {"low_load": run_serve(torch, rate=50000.0),
-                           "near_saturation": run_serve(torch, rate=200000.0)}
+                           "near_saturation": run_serve(torch, rate=800000.0)}
         extras["other_variant"] = run_variant(torch, not bottom_up, ipt=args.ipt)
         extras["apps"] = run_apps(torch)
     cpu = cpu_jobs.result() if cpu_jobs is not None else None

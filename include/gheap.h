@@ -391,6 +391,27 @@ int heapring_take(gheap_ring_t r, uint32_t n, const uint64_t *ids, void *host_ou
 /* Requests submitted and not yet taken. */
 int heapring_pending(gheap_ring_t r, uint64_t *in_flight);
 
+/* A whole serving session on a running ring, the host loop in native code:
+ * request i arrives at arrival[i] seconds after the call starts (ascending;
+ * with realtime = 0 all have arrived at the start), names heap heaps[i] (a
+ * bound heap of the set), kind kinds[i] and size sizes[i]; `keys` holds the
+ * inserts' keys back to back in request order.  Each heap takes its requests
+ * in arrival order, several in flight at once.  An insert that could take its
+ * heap past capacities[h] keys (held[h] = keys the heap holds at the start,
+ * updated as the session runs) waits while earlier requests of that heap are
+ * in flight and is refused with GHEAP_ERR_FULL when none are; one larger than
+ * the heap, or a request larger than a key arena, is refused at once.  Out:
+ * each deleteMin's keys (ascending) at out[sum of the sizes of the deleteMins
+ * before it], out_counts[i] (keys returned, or n for an insert), t_submit[i]
+ * and t_done[i] (seconds from the start when it entered the ring and when its
+ * completion was seen; -1 if it never entered) and status[i].  Returns when
+ * every request is done, or GHEAP_ERR_TIMEOUT when nothing completed for 60
+ * s while requests were in flight. */
+int heapring_serve(gheap_ring_t r, uint64_t n_req, const double *arrival, const uint32_t *heaps,
+                   const uint32_t *kinds, const uint64_t *sizes, const void *keys,
+                   const uint64_t *capacities, uint64_t *held, int realtime, void *out,
+                   uint64_t *out_counts, double *t_submit, double *t_done, int32_t *status);
+
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is an
  * interface for callers that must not allocate device memory -- code whose

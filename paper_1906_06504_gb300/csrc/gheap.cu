@@ -10,7 +10,11 @@
 #include <string.h>
 
 #include <atomic>
+#include <chrono>
+#include <deque>
 #include <mutex>
+#include <thread>
+#include <vector>
 
 #include "gheap.h"
 #include "gheap_kernel.cuh"
@@ -1254,71 +1258,99 @@ int heapring_stop(gheap_ring_t r)
     return err ? GHEAP_ERR_TIMEOUT : GHEAP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Appends one request (not yet published).  Returns 1 when appended (id in
+// *id), 0 when the ring, an arena or the request slots are full, or
+// GHEAP_ERR_ARG for a malformed request.
+int ring_append(gheap_ring_t r, uint32_t h, uint32_t kind, uint64_t n, const unsigned char *src,
+                uint64_t *id)
+{
+    gheapset_t S = r->set;
+    const uint32_t k = S->k;
+    const size_t kb = S->key_bytes;
+    if (h >= S->n || !S->heaps[h] || n == 0 || (kind != GHEAP_OP_INS && kind != GHEAP_OP_DEL) ||
+        (kind == GHEAP_OP_INS && !src))
+        return GHEAP_ERR_ARG;
+    if (r->next_seq - r->oldest >= r->n_slots) return 0;
+    const uint64_t n_ops = (n + k - 1) / k;
+    if (r->op_tail + n_ops - r->op_free > r->op_cap) return 0;
+    uint64_t in_pos = 0, out_pos = 0;
+    uint64_t in_tail = r->in_tail, out_tail = r->out_tail;
+    if (kind == GHEAP_OP_INS) {
+        in_pos = arena_take(in_tail, r->in_free, r->in_cap, n);
+        if (in_pos == UINT64_MAX) return 0;
+    } else {
+        out_pos = arena_take(out_tail, r->out_free, r->out_cap, n);
+        if (out_pos == UINT64_MAX) return 0;
+    }
+    const uint64_t seq = r->next_seq;
+    const uint32_t slot = (uint32_t)(seq % r->n_slots);
+    RingReq &q = r->reqs[slot];
+    q.seq = seq;
+    q.heap = h;
+    q.kind = kind;
+    q.n = n;
+    q.in_start = kind == GHEAP_OP_INS ? in_pos : r->in_tail;
+    q.in_end = in_tail;
+    q.out_start = kind == GHEAP_OP_DEL ? out_pos : r->out_tail;
+    q.out_end = out_tail;
+    r->in_tail = in_tail;
+    r->out_tail = out_tail;
+    r->req_ops[slot] = (uint32_t)n_ops;
+    r->req_seq[slot] = seq;
+    r->req_base[slot] = kind == GHEAP_OP_DEL ? out_pos % r->out_cap : 0;
+    if (kind == GHEAP_OP_INS) memcpy(r->in_keys + (in_pos % r->in_cap) * kb, src, n * kb);
+    for (uint64_t j = 0; j < n_ops; j++) {
+        gh::RingOp &o = r->ops[r->op_tail % r->op_cap];
+        const uint32_t m = (uint32_t)(n - j * k < k ? n - j * k : k);
+        o.heap = h;
+        o.kind_n = (kind << 24) | (kind == GHEAP_OP_DEL ? GHEAPSET_CURSOR : 0u) | m;
+        o.offset = kind == GHEAP_OP_INS ? in_pos % r->in_cap + j * k : slot;
+        o.ticket = r->heap_ticket[h]++;
+        o.req = slot;
+        o._pad = 0;
+        r->op_tail++;
+    }
+    q.op_end = r->op_tail;
+    q.state = RQ_INFLIGHT;
+    r->next_seq++;
+    *id = seq;
+    return 1;
+}
+
+// Publishes every appended entry: one release store of the tail after them.
+void ring_publish(gheap_ring_t r)
+{
+    __atomic_store_n(r->tail, (unsigned long long)r->op_tail, __ATOMIC_RELEASE);
+}
+
+}  // namespace
+
+extern "C" {
+
 int heapring_submit(gheap_ring_t r, uint32_t n_req, const uint32_t *heaps, const uint32_t *kinds,
                     const uint64_t *sizes, const void *keys, uint64_t *ids)
 {
     if (!r || (n_req && (!heaps || !kinds || !sizes))) return GHEAP_ERR_ARG;
-    gheapset_t S = r->set;
-    const uint32_t k = S->k;
-    const size_t kb = S->key_bytes;
+    const size_t kb = r->set->key_bytes;
     const unsigned char *src = static_cast<const unsigned char *>(keys);
     uint32_t i = 0;
     for (; i < n_req; i++) {
-        const uint32_t h = heaps[i], kind = kinds[i];
-        const uint64_t n = sizes[i];
-        if (h >= S->n || !S->heaps[h] || n == 0 || (kind != GHEAP_OP_INS && kind != GHEAP_OP_DEL) ||
-            (kind == GHEAP_OP_INS && !src))
-            return i ? (int)i : GHEAP_ERR_ARG;
-        if (r->next_seq - r->oldest >= r->n_slots) break;
-        const uint64_t n_ops = (n + k - 1) / k;
-        if (r->op_tail + n_ops - r->op_free > r->op_cap) break;
-        uint64_t in_pos = 0, out_pos = 0;
-        uint64_t in_tail = r->in_tail, out_tail = r->out_tail;
-        if (kind == GHEAP_OP_INS) {
-            in_pos = arena_take(in_tail, r->in_free, r->in_cap, n);
-            if (in_pos == UINT64_MAX) break;
-        } else {
-            out_pos = arena_take(out_tail, r->out_free, r->out_cap, n);
-            if (out_pos == UINT64_MAX) break;
+        uint64_t id = 0;
+        const int rc = ring_append(r, heaps[i], kinds[i], sizes[i],
+                                   kinds[i] == GHEAP_OP_INS ? src : nullptr, &id);
+        if (rc < 0) {
+            if (i == 0) return rc;
+            break;
         }
-        const uint64_t seq = r->next_seq;
-        const uint32_t slot = (uint32_t)(seq % r->n_slots);
-        RingReq &q = r->reqs[slot];
-        q.seq = seq;
-        q.heap = h;
-        q.kind = kind;
-        q.n = n;
-        q.in_start = kind == GHEAP_OP_INS ? in_pos : r->in_tail;
-        q.in_end = in_tail;
-        q.out_start = kind == GHEAP_OP_DEL ? out_pos : r->out_tail;
-        q.out_end = out_tail;
-        r->in_tail = in_tail;
-        r->out_tail = out_tail;
-        r->req_ops[slot] = (uint32_t)n_ops;
-        r->req_seq[slot] = seq;
-        r->req_base[slot] = kind == GHEAP_OP_DEL ? out_pos % r->out_cap : 0;
-        if (kind == GHEAP_OP_INS) {
-            memcpy(r->in_keys + (in_pos % r->in_cap) * kb, src, n * kb);
-            src += n * kb;
-        }
-        for (uint64_t j = 0; j < n_ops; j++) {
-            gh::RingOp &o = r->ops[r->op_tail % r->op_cap];
-            const uint32_t m = (uint32_t)(n - j * k < k ? n - j * k : k);
-            o.heap = h;
-            o.kind_n = (kind << 24) | (kind == GHEAP_OP_DEL ? GHEAPSET_CURSOR : 0u) | m;
-            o.offset = kind == GHEAP_OP_INS ? in_pos % r->in_cap + j * k : slot;
-            o.ticket = r->heap_ticket[h]++;
-            o.req = slot;
-            o._pad = 0;
-            r->op_tail++;
-        }
-        q.op_end = r->op_tail;
-        q.state = RQ_INFLIGHT;
-        r->next_seq++;
-        if (ids) ids[i] = seq;
+        if (rc == 0) break;
+        if (kinds[i] == GHEAP_OP_INS) src += sizes[i] * kb;
+        if (ids) ids[i] = id;
     }
-    // publish: every entry and key written above before the new tail
-    __atomic_store_n(r->tail, (unsigned long long)r->op_tail, __ATOMIC_RELEASE);
+    ring_publish(r);
     return (int)i;
 }
 
@@ -1382,6 +1414,167 @@ int heapring_pending(gheap_ring_t r, uint64_t *in_flight)
 {
     if (!r || !in_flight) return GHEAP_ERR_ARG;
     *in_flight = r->next_seq - r->oldest;
+    return GHEAP_OK;
+}
+
+int heapring_serve(gheap_ring_t r, uint64_t n_req, const double *arrival, const uint32_t *heaps,
+                   const uint32_t *kinds, const uint64_t *sizes, const void *keys,
+                   const uint64_t *capacities, uint64_t *held, int realtime, void *out,
+                   uint64_t *out_counts, double *t_submit, double *t_done, int32_t *status)
+{
+    if (!r || (n_req && (!arrival || !heaps || !kinds || !sizes || !capacities || !held ||
+                         !out_counts || !t_submit || !t_done || !status)))
+        return GHEAP_ERR_ARG;
+    if (!r->running) return GHEAP_ERR_ARG;
+    gheapset_t S = r->set;
+    const uint32_t nh = S->n;
+    const size_t kb = S->key_bytes;
+    const unsigned char *in = static_cast<const unsigned char *>(keys);
+    unsigned char *dst = static_cast<unsigned char *>(out);
+    // each insert's keys and each deleteMin's output place, in request order
+    std::vector<uint64_t> key_off(n_req), out_off(n_req);
+    uint64_t ko = 0, oo = 0;
+    for (uint64_t i = 0; i < n_req; i++) {
+        key_off[i] = ko;
+        out_off[i] = oo;
+        if (kinds[i] == GHEAP_OP_INS) ko += sizes[i];
+        else oo += sizes[i];
+        out_counts[i] = 0;
+        t_submit[i] = t_done[i] = -1.0;
+        status[i] = GHEAP_OK;
+    }
+    std::vector<std::deque<uint64_t>> queue(nh);
+    std::vector<uint64_t> busy(nh, 0);
+    std::vector<uint8_t> blocked(nh, 0), listed(nh, 0);
+    std::deque<uint32_t> ready;             // heaps with queued requests, not blocked
+    const uint64_t base = r->next_seq;      // ids from here on are this call's submissions
+    std::vector<uint64_t> req_of;           // request index of id base + j
+    req_of.reserve(n_req);
+    std::vector<uint64_t> ids(r->n_slots), counts(r->n_slots);
+    std::vector<int32_t> sts(r->n_slots);
+    const uint64_t arena = r->in_cap < r->out_cap ? r->in_cap : r->out_cap;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto now_s = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    uint64_t next = 0, done = 0, inflight = 0;
+    double last_progress = 0.0;
+    auto finish = [&](uint64_t i, int32_t st, double t) {
+        status[i] = st;
+        t_done[i] = t;
+        done++;
+    };
+    while (done < n_req) {
+        double now = now_s();
+        bool progress = false;
+        // arrivals, in order
+        while (next < n_req && (!realtime || arrival[next] <= now)) {
+            const uint32_t h = heaps[next];
+            if (h >= nh || !S->heaps[h] || sizes[next] == 0 ||
+                (kinds[next] != GHEAP_OP_INS && kinds[next] != GHEAP_OP_DEL)) {
+                finish(next, GHEAP_ERR_ARG, now);
+            } else {
+                queue[h].push_back(next);
+                if (!listed[h] && !blocked[h]) {
+                    listed[h] = 1;
+                    ready.push_back(h);
+                }
+            }
+            next++;
+            progress = true;
+        }
+        // completions: take each deleteMin's keys into its place
+        uint32_t nd = 0;
+        heapring_poll(r, ids.data(), counts.data(), sts.data(), r->n_slots, &nd);
+        now = now_s();
+        for (uint32_t j = 0; j < nd; j++) {
+            const uint64_t i = req_of[ids[j] - base];
+            const uint32_t h = heaps[i];
+            uint64_t got = 0;
+            heapring_take(r, 1, &ids[j], kinds[i] == GHEAP_OP_DEL ? dst + out_off[i] * kb : nullptr,
+                          kinds[i] == GHEAP_OP_DEL ? sizes[i] : 0, &got);
+            out_counts[i] = kinds[i] == GHEAP_OP_DEL ? got : sizes[i];
+            if (kinds[i] == GHEAP_OP_DEL) held[h] -= got;
+            busy[h]--;
+            inflight--;
+            if (blocked[h]) {
+                blocked[h] = 0;
+                if (!queue[h].empty() && !listed[h]) {
+                    listed[h] = 1;
+                    ready.push_back(h);
+                }
+            }
+            finish(i, sts[j], now);
+            progress = true;
+        }
+        // submissions: every ready heap's queue in order, until one must wait
+        bool appended = false, full = false;
+        for (size_t round = ready.size(); round > 0 && !full; --round) {
+            const uint32_t h = ready.front();
+            ready.pop_front();
+            listed[h] = 0;
+            auto &qh = queue[h];
+            while (!qh.empty()) {
+                const uint64_t i = qh.front();
+                const uint64_t n = sizes[i];
+                const bool ins = kinds[i] == GHEAP_OP_INS;
+                if (n > arena || (ins && n > capacities[h])) {
+                    qh.pop_front();
+                    finish(i, ins && n > capacities[h] ? GHEAP_ERR_FULL : GHEAP_ERR_ARG, now);
+                    continue;
+                }
+                if (ins && held[h] + n > capacities[h]) {
+                    if (busy[h] == 0) {
+                        // nothing ahead of it can make room: refuse it
+                        qh.pop_front();
+                        finish(i, GHEAP_ERR_FULL, now);
+                        continue;
+                    }
+                    blocked[h] = 1;        // waits for this heap's completions
+                    break;
+                }
+                uint64_t id = 0;
+                const int rc = ring_append(r, h, kinds[i], n, ins ? in + key_off[i] * kb : nullptr,
+                                           &id);
+                if (rc < 0) {
+                    qh.pop_front();
+                    finish(i, rc, now);
+                    continue;
+                }
+                if (rc == 0) {
+                    full = true;           // the ring is full: retry after completions
+                    break;
+                }
+                qh.pop_front();
+                req_of.push_back(i);
+                t_submit[i] = now;
+                if (ins) held[h] += n;
+                busy[h]++;
+                inflight++;
+                appended = true;
+            }
+            if (!qh.empty() && !blocked[h] && !listed[h]) {
+                listed[h] = 1;
+                ready.push_back(h);
+            }
+        }
+        if (appended) {
+            ring_publish(r);
+            progress = true;
+        }
+        if (progress) {
+            last_progress = now;
+            continue;
+        }
+        if (inflight == 0 && ready.empty() && next < n_req && realtime) {
+            // idle until the next arrival
+            const double wait = arrival[next] - now_s();
+            if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+            last_progress = now_s();
+            continue;
+        }
+        if (now - last_progress > 60.0) return GHEAP_ERR_TIMEOUT;
+    }
     return GHEAP_OK;
 }
 

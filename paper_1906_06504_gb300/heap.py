@@ -98,6 +98,8 @@ def lib():
             "heapring_poll": (ctypes.c_int, [vp, vp, vp, vp, u32, u32p]),
             "heapring_take": (ctypes.c_int, [vp, u32, vp, vp, u64, vp]),
             "heapring_pending": (ctypes.c_int, [vp, u64p]),
+            "heapring_serve": (ctypes.c_int, [vp, u64, vp, vp, vp, vp, vp, vp, vp, ctypes.c_int,
+                                              vp, vp, vp, vp, vp]),
             "heap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             # gheap_apps.h
             "sssp_create": (ctypes.c_int, [ctypes.POINTER(vp), u32, u64, u32, u32, u64]),
@@ -499,6 +501,31 @@ class GHeapRing:
         v = ctypes.c_uint64()
         _check(lib().heapring_pending(self._r, ctypes.byref(v)), "heapring_pending")
         return int(v.value)
+
+    def serve(self, arrival, heaps, kinds, sizes, keys, capacities, held, realtime=True):
+        """A whole session in the native host loop (heapring_serve).  Returns
+        (out keys back to back, out_counts, t_submit, t_done, status); `held`
+        (uint64 per heap) is updated in place."""
+        n = len(sizes)
+        arrival = np.ascontiguousarray(arrival, dtype=np.float64)
+        heaps = np.ascontiguousarray(heaps, dtype=np.uint32)
+        kinds = np.ascontiguousarray(kinds, dtype=np.uint32)
+        sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+        keys = np.ascontiguousarray(keys if keys is not None else np.zeros(1, self.key_dtype),
+                                    dtype=self.key_dtype)
+        capacities = np.ascontiguousarray(capacities, dtype=np.uint64)
+        assert held.dtype == np.uint64 and held.flags["C_CONTIGUOUS"]
+        out = np.empty(max(1, int(sizes[kinds == 2].sum())), dtype=self.key_dtype)
+        counts = np.zeros(n, dtype=np.uint64)
+        t_sub = np.zeros(n, dtype=np.float64)
+        t_done = np.zeros(n, dtype=np.float64)
+        status = np.zeros(n, dtype=np.int32)
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(lib().heapring_serve(self._r, n, ptr(arrival), ptr(heaps), ptr(kinds), ptr(sizes),
+                                    ptr(keys), ptr(capacities), ptr(held), 1 if realtime else 0,
+                                    ptr(out), ptr(counts), ptr(t_sub), ptr(t_done), ptr(status)),
+               "heapring_serve")
+        return out, counts, t_sub, t_done, status
 
     def close(self):
         if getattr(self, "_r", None):

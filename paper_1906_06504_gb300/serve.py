@@ -229,10 +229,74 @@ class HeapServer:
         self.stats["requests"] += int(ids.size)
         return int(ids.size)
 
-    def run(self, requests, realtime=True):
+    def run(self, requests, realtime=True, native=True):
         """Serves `requests` (arrival times in seconds from the start).  With
-        realtime=False every request is treated as already arrived."""
+        realtime=False every request is treated as already arrived.  With
+        native=True, and every heap the requests name admitted up front, the
+        host loop runs in native code (heapring_serve) under the same rules;
+        else in Python (admitting and evicting heaps as requests come)."""
         reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        if native and self._admit_all({r.heap for r in reqs if 0 <= r.heap < self.n_heaps}):
+            return self._run_native(reqs, realtime)
+        return self._run_python(reqs, realtime)
+
+    def _admit_all(self, heaps):
+        for h in sorted(heaps):
+            if self.heaps[h] is None and not self._admit(h, heaps):
+                return False
+        return all(self.heaps[h] is not None for h in heaps)
+
+    def _run_native(self, reqs, realtime):
+        n = len(reqs)
+        arrival = np.array([r.arrival for r in reqs], dtype=np.float64)
+        heaps = np.array([r.heap for r in reqs], dtype=np.uint32)
+        kinds = np.array([OP_INS if r.kind == "ins" else OP_DEL for r in reqs], dtype=np.uint32)
+        sizes = np.array([r.n for r in reqs], dtype=np.uint64)
+        ins = [np.asarray(r.keys, dtype=self.np_key) for r in reqs if r.kind == "ins"]
+        keys = np.concatenate(ins) if ins else None
+        held = np.array(self.size, dtype=np.uint64)
+        self.ring.start()
+        try:
+            out, counts, t_sub, t_done, status = self.ring.serve(
+                arrival, heaps, kinds, sizes, keys, self.capacities, held, realtime)
+        finally:
+            self.ring.stop()
+        self.size = [int(x) for x in held]
+        dels = kinds == OP_DEL
+        off = np.concatenate([[0], np.cumsum(np.where(dels, sizes, 0))[:-1]]).astype(np.int64)
+        for i, r in enumerate(reqs):
+            st = int(status[i])
+            r.t_submit = float(t_sub[i]) if t_sub[i] >= 0 else None
+            r.t_done = float(t_done[i])
+            r.latency = r.t_done - r.arrival
+            if st != 0 and r.t_submit is not None:
+                r.error = "device error %d on heap %d" % (st, r.heap)
+            elif st != 0:
+                r.error = self._refusal(r, st)
+            if r.kind == "del" and st == 0:
+                r.result = out[off[i]:off[i] + int(counts[i])]
+        # requests in flight when each one entered the ring
+        sub = np.sort(t_sub[t_sub >= 0])
+        done = np.sort(t_done[t_sub >= 0])
+        at = np.searchsorted(sub, sub, side="right") - np.searchsorted(done, sub, side="right")
+        self.stats["requests"] += n
+        self.stats["refused"] += int(np.count_nonzero(t_sub < 0))
+        self.stats["max_inflight"] = max(self.stats["max_inflight"], int(at.max()) if at.size else 0)
+        self.stats["submitted_while_busy"] += int(np.count_nonzero(at > 1))
+        self.stats["submits"] += 1
+        return reqs
+
+    def _refusal(self, r, code):
+        """Why the native loop refused request r (its status `code`)."""
+        why = self._refuse_reason(r)
+        if why is not None:
+            return why
+        if code == -3:
+            return "heap %d full: insert of %d keys, capacity %d" % (
+                r.heap, r.n, self.capacities[r.heap])
+        return "refused (%d)" % code
+
+    def _run_python(self, reqs, realtime):
         pending = collections.deque()
         inflight = {}
         nxt = 0
