@@ -191,7 +191,7 @@ int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k,
  * (Section 4.3).  The map is its own inverse. */
 uint64_t heap_slot_to_node(uint64_t j);
 
-/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 22:
+/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 23:
  * out[0] node loads, out[1] node stores, out[2] merges, out[3] merges skipped
  * as disjoint (Section 4.3), out[4] INS ops, out[5] DEL ops, out[6] lock
  * waits that spun, out[7] sum of root-hold time in ns; then SM cycles seen
@@ -201,7 +201,8 @@ uint64_t heap_slot_to_node(uint64_t j);
  * wait [15], INS batch sort [16], INS node-lock waits [17], INS level steps
  * [18], INS levels [19]; DELs that received the keys of an INS whose target
  * they had marked (Section 3.3.2) [20], root hand-backs of DELs waiting for
- * such an INS (heap_set_yields) [21]. */
+ * such an INS (heap_set_yields) [21], children a DEL found reserved as the
+ * target of an INS still on its way down and treated as absent [22]. */
 int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
 
 /* Test hook for the bounded waits: marks the root lock as held, with no

@@ -3,7 +3,7 @@
  * 5.2): the C++ standard library's priority queue (a binary heap over a
  * vector), used as a min-queue of 32-bit keys.
  *
- * TEST AND BASELINE INFRASTRUCTURE ONLY, like the rest of this directory:
+ * Test and CPU-baseline infrastructure only, like the rest of this directory:
  * only the tests and the CPU-baseline legs of bench.py load it.  It shares
  * nothing with the CUDA implementation.
  *

@@ -123,7 +123,8 @@ enum : uint32_t {
     STAT_INS_LEVELS = 19,       // levels visited
     STAT_DELIVERIES = 20,       // DELs that received a marked target's keys (Section 3.3.2)
     STAT_DEL_YIELDS = 21,       // DELs that handed the root back to let an INS land first
-    N_STATS = 22
+    STAT_TARGET_CHILDREN = 22,  // children a DEL found reserved by an INS in flight (absent)
+    N_STATS = 23
 };
 
 // Root word: bits 0-29 m (full nodes), bits 30-41 s (partial-buffer keys),
@@ -1899,7 +1900,12 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
             }
         } while (__any_sync(0xffffffffu, pending));
     }
-    if (lane < 2) lk[lane] = v;
+    if (lane < 2) {
+        lk[lane] = v;
+        // the target of an INS still on its way down counts as absent here
+        if (v == ST_TARGET || v == ST_MARKED || v == ST_DELIVERED)
+            stat_add(sh, STAT_TARGET_CHILDREN, 1);
+    }
     __syncwarp();
     if (lk[0] == ST_AVAIL) g2s(dl, node_keys(H, sl, k), k, lane, 32u);
     if (lk[1] == ST_AVAIL) g2s(dr, node_keys(H, sr, k), k, lane, 32u);

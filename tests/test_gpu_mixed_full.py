@@ -6,7 +6,10 @@ device at once -- the heap is 14 levels deep.  The GPU records the order in
 which operations held the root; replaying that order through the textbook
 binary heap fixes every DEL output (Section 3.3.3, Theorem 1), and every one
 of the 2^16 DELs must match it bit for bit.  Properties 1-3 (Section 3.1)
-must hold on the heap left at the end.  With yields = 0 (the paper's INS/DEL
+must hold on the heap left at the end.  A DEL treats a child that an INS
+still on its way down has reserved as absent (that INS merges with the
+child's parent before it fills the child); the counters show such children
+were met, and the replay shows the results stayed exact.  With yields = 0 (the paper's INS/DEL
 cooperation of Section 3.3.2: a DEL whose last node is an INS target still
 in flight marks it and waits, holding the root, for the keys) the device
 counters must show that such deliveries happened at this depth.
@@ -54,8 +57,12 @@ def test_config2_mixed_full_size_replay(yields):
         assert r.replay_and_compare() == n_pairs
         check_properties(h)
         deliveries = st["deliveries"] - before["deliveries"]
+        absent = st["target_children"] - before["target_children"]
         if yields == 0:
-            assert deliveries > 0, st
-        print("yields=%d: %d deliveries, %d root hand-backs, %d DEL levels"
-              % (yields, deliveries, st["del_yields"] - before["del_yields"],
-                 st["del_levels"] - before["del_levels"]))
+            # the hand-off ran, and DELs sifted past children that in-flight
+            # INSs had reserved (treated as absent: each such INS merges with
+            # the child's parent before it fills the child)
+            assert deliveries > 0 and absent > 0, st
+        print("yields=%d: %d deliveries, %d root hand-backs, %d reserved children passed, "
+              "%d DEL levels" % (yields, deliveries, st["del_yields"] - before["del_yields"],
+                                 absent, st["del_levels"] - before["del_levels"]))
