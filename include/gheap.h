@@ -333,7 +333,9 @@ int heapset_graph_destroy(gheapset_graph_t g);
  * flight per heap, up to the ring's limits.  Heaps of the set must be driven
  * only through the ring while it runs, and no other launch on the set may
  * overlap it.  Heap memory must not be freed (heapset_unbind, heap_destroy)
- * while the ring runs: stop it first.
+ * while the ring runs: stop it first, and destroy the ring before its set.
+ * A ring is driven by one host thread at a time (its host-side bookkeeping
+ * takes no lock).
  * ------------------------------------------------------------------------ */
 typedef struct gheap_ring_s *gheap_ring_t;
 

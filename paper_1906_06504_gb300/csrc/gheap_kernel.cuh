@@ -2538,8 +2538,10 @@ __device__ __forceinline__ RingOp ld_ring_op(const RingOp *e)
 template <typename K>
 __device__ void ring_complete(const Params<K> &p, uint32_t req, uint32_t status)
 {
-    __threadfence_system();   // the operation's output reaches the host first
+    // the operation's error bits and its output come before its count: the
+    // block that counts the request's last operation then sees both
     if (status) atomicOr(p.ring_status + req, status);
+    __threadfence_system();
     const uint32_t n_ops = __ldcv(p.ring_req_ops + req);
     const uint32_t done = atomicAdd(p.ring_ops_done + req, 1u) + 1u;
     if (done != n_ops) return;
