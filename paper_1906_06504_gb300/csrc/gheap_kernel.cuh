@@ -275,6 +275,10 @@ struct Shared {
     int halt;                 // DEL: the sift ends after MergeAndSort(l, r)
     int swap;                 // DEL: MergeAndSort(cur, small child) is a swap
     uint32_t lk[2][2];        // lock results, double-buffered by level
+    // delete-only launches: the mbarriers of the root step's TMA fetches
+    // (level 1, the last node), the fetches issued on each and seen landed
+    unsigned long long l1_mbar, last_mbar;
+    uint32_t l1_arms, l1_seen, last_arms, last_seen;
     // release ring: posted by merge thread 0, taken in order by the release
     // warp (`rq_read`: requests taken, their slots free again)
     RelReq rq[N_REQ];
@@ -331,6 +335,56 @@ __device__ __forceinline__ void st_release_cta(uint32_t *p, uint32_t v)
 // ---------------------------------------------------------------------------
 // memory-model helpers
 // ---------------------------------------------------------------------------
+
+// mbarrier and TMA bulk copies (global -> shared, completion counted in
+// bytes on the mbarrier).  Addresses 16-byte aligned, sizes multiples of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+// One test (suspending for at most a hardware-bounded time) that the phase
+// of parity `par` has completed.
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, uint32_t par)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred q;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(b)), "r"(par) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            unsigned long long *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+
+// Orders this thread's generic-proxy accesses of global memory (the lock
+// acquisitions, and what they made visible) with its later async-proxy ones
+// (the TMA reads of the nodes).  The shared buffers need none: their last
+// readers finished before a barrier that precedes the copy.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -598,6 +652,38 @@ template <typename K>
 __device__ __forceinline__ void set_err(const HeapView<K> &H, uint32_t e)
 {
     atomicCAS(&H.hdr->err, E_NONE, e);
+}
+
+// A TMA fetch of n held nodes (slots s0, s1) into a, b, completing on the
+// mbarrier `mb` (arms: fetches issued on it).  One thread, after the locks.
+template <typename K>
+__device__ __forceinline__ void tma_fetch(const HeapView<K> &H, uint32_t k, uint32_t n,
+                                          uint32_t s0, K *a, uint32_t s1, K *b,
+                                          unsigned long long *mb, uint32_t &arms)
+{
+    const uint32_t bytes = k * (uint32_t)sizeof(K);
+    fence_proxy_async_global();
+    mbar_arrive_expect_tx(mb, n * bytes);
+    tma_load_1d(a, node_keys(H, s0, k), bytes, mb);
+    if (n > 1) tma_load_1d(b, node_keys(H, s1, k), bytes, mb);
+    ++arms;
+}
+
+// Waits (bounded by the heap's timeout) until the last fetch issued on `mb`
+// has landed.  False: gave up (the heap's sticky error is set).
+template <typename K>
+__device__ bool tma_land(const Params<K> &p, const HeapView<K> &H, unsigned long long *mb,
+                         uint32_t arms, uint32_t &seen)
+{
+    if (seen == arms) return true;
+    const uint32_t par = (arms - 1u) & 1u;
+    unsigned long long t0 = 0;
+    uint32_t it = 0;
+    while (!mbar_try_wait(mb, par)) {
+        if (!wait_ok(p, H, t0, it)) return false;
+    }
+    seen = arms;
+    return true;
 }
 
 // Merge thread 0 (the only writer of rq_posted), after a barrier that follows
@@ -1866,13 +1952,11 @@ __device__ bool bu_rise(const Params<K> &p, const HeapView<K> &H, Shared &sh, K 
 // per poll, each poll a compare-and-swap that also takes the lock), so that it
 // is converged when it issues the copies.
 template <typename K>
-__device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapView<K> &H,
-                                                 Shared &sh, uint32_t sl, uint32_t sr,
-                                                 uint32_t first0, uint32_t first1, K *dl, K *dr,
-                                                 uint32_t *lk)
+__device__ __forceinline__ void cw_lock_two(const Params<K> &p, const HeapView<K> &H, Shared &sh,
+                                            uint32_t sl, uint32_t sr, uint32_t first0,
+                                            uint32_t first1, uint32_t *lk)
 {
     const uint32_t lane = clane();
-    const uint32_t k = p.k;
     uint32_t v = ST_EMPTY;
     uint32_t *w = nullptr;
     if (lane < 2) {
@@ -1907,6 +1991,17 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
             stat_add(sh, STAT_TARGET_CHILDREN, 1);
     }
     __syncwarp();
+}
+
+template <typename K>
+__device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapView<K> &H,
+                                                 Shared &sh, uint32_t sl, uint32_t sr,
+                                                 uint32_t first0, uint32_t first1, K *dl, K *dr,
+                                                 uint32_t *lk)
+{
+    const uint32_t lane = clane();
+    const uint32_t k = p.k;
+    cw_lock_two(p, H, sh, sl, sr, first0, first1, lk);
     if (lk[0] == ST_AVAIL) g2s(dl, node_keys(H, sl, k), k, lane, 32u);
     if (lk[1] == ST_AVAIL) g2s(dr, node_keys(H, sr, k), k, lane, 32u);
     cp_async_commit();
@@ -1919,7 +2014,7 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
 // `out_off`.  Six smem buffers rotate between the roles current node, left
 // and right child, and three free ones.  Returns false when the block must
 // stop.
-template <typename K, int IPT>
+template <typename K, int IPT, bool TMA = false>
 __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t want, unsigned long long out_off, unsigned long long ref,
                        uint32_t *count_out, long long req)
@@ -2042,7 +2137,50 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     } else if (!root_gone) {
         uint32_t sl, sr;
         child_slots(1, H.max_nodes, sl, sr);
-        if (need_last) {
+        if (TMA && m >= 16u && (k * (uint32_t)sizeof(K)) % 16u == 0) {
+            // the root step of delete-only launches: level 1 fetched by TMA
+            // the moment both locks are held, the last node (below level 3:
+            // the top four levels are full) as soon as it is taken -- one
+            // thread each, instead of the warp's copies after both locks
+            // (nodes of a multiple of 16 bytes: the buffers and the node
+            // addresses are then 16-byte aligned, as the copies require)
+            uint32_t *lw = need_last ? node_state(H, m) : nullptr;
+            uint32_t t = ST_EMPTY;
+            if (lane < 2) t = try_lock(node_state(H, lane ? sr : sl));
+            if (lane == 2 && lw) t = try_lock(lw);
+            const uint32_t c0 = __shfl_sync(0xffffffffu, t, 0);
+            const uint32_t c1 = __shfl_sync(0xffffffffu, t, 1);
+            const uint32_t tl = __shfl_sync(0xffffffffu, t, 2);
+            const bool l1_now = c0 == ST_AVAIL && c1 == ST_AVAIL;
+            if (l1_now && lane == 0)
+                tma_fetch(H, k, 2u, sl, PB(il), sr, PB(ir), &sh.l1_mbar, sh.l1_arms);
+            if (lw && lane == 2) {
+                if (take_last(p, H, sh, lw, tl)) {
+                    st_relaxed(lw, ST_EMPTY);
+                    tma_fetch(H, k, 1u, m, PB(f1), 0u, PB(f1), &sh.last_mbar, sh.last_arms);
+                } else {
+                    sh.abort = 1;
+                }
+            }
+            __syncwarp();
+            if (!l1_now) {
+                // the DEL ahead still holds level 1: wait for both locks
+                cw_lock_two(p, H, sh, sl, sr, c0, c1, sh.lk[0]);
+                if (lane == 0 && sh.lk[0][0] == ST_AVAIL && sh.lk[0][1] == ST_AVAIL)
+                    tma_fetch(H, k, 2u, sl, PB(il), sr, PB(ir), &sh.l1_mbar, sh.l1_arms);
+            } else if (lane == 0) {
+                sh.lk[0][0] = sh.lk[0][1] = ST_AVAIL;
+            }
+            if (lane == 0 && sh.lk[0][0] == ST_AVAIL && sh.lk[0][1] == ST_AVAIL) {
+                if (!tma_land(p, H, &sh.l1_mbar, sh.l1_arms, sh.l1_seen))
+                    sh.lk[0][0] = sh.lk[0][1] = ST_GAVE_UP;
+                stat_add(sh, STAT_LOADS, 2);
+            }
+            if (lw && lane == 2 && !sh.abort &&
+                !tma_land(p, H, &sh.last_mbar, sh.last_arms, sh.last_seen))
+                sh.abort = 1;
+            __syncwarp();
+        } else if (need_last) {
             uint32_t *lw = node_state(H, m);
             if (m <= 3) {
                 // the last node is a child of the root: take it first, then
@@ -2601,6 +2739,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         sh.stats_on = p.stats != nullptr;
         sh.use_fixed = 0;
         rel_exited = 0;
+        sh.l1_arms = sh.l1_seen = sh.last_arms = sh.last_seen = 0;
+        if (DEL_ONLY) {
+            mbar_init(&sh.l1_mbar, 1u);
+            mbar_init(&sh.last_mbar, 1u);
+        }
     }
     bar_block();
     if (is_rel()) {
@@ -2704,7 +2847,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         }
         const bool listed = !DEL_ONLY && (p.mode == MODE_OPS || multi);
         if constexpr (DEL_ONLY) {
-            ok = del_op<K, IPT>(p, H, sh, base, n, off, op, nullptr, -1ll);
+            ok = del_op<K, IPT, true>(p, H, sh, base, n, off, op, nullptr, -1ll);
             if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
         } else if (kind == GHEAP_OP_INS) {
             // stage and sort the batch before taking the root (Section 4.1)
@@ -2768,6 +2911,19 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
             st_release_cta(&sh.rq_posted, sh.rq_posted + 1);
         }
         spin_until(&rel_exited, 1u, tmo);
+        if (DEL_ONLY) {
+            // no fetch may still be landing in this block's shared memory
+            // when it leaves (one that was given up on: bounded again)
+            const unsigned long long t0 = gtimer();
+            if (sh.l1_seen != sh.l1_arms)
+                while (!mbar_try_wait(&sh.l1_mbar, (sh.l1_arms - 1u) & 1u) &&
+                       gtimer() - t0 < 1000000000ull) {
+                }
+            if (sh.last_seen != sh.last_arms)
+                while (!mbar_try_wait(&sh.last_mbar, (sh.last_arms - 1u) & 1u) &&
+                       gtimer() - t0 < 2000000000ull) {
+                }
+        }
     }
     bar_all();
     if (p.stats && threadIdx.x < N_STATS && sh.cnt[threadIdx.x])
