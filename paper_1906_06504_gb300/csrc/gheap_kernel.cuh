@@ -285,6 +285,10 @@ struct Shared {
     uint32_t rq_posted, rq_read;
     uint32_t stats_on;        // the launch counts statistics
     unsigned long long cnt[N_STATS];
+    // launches other than delete-only: the mbarrier of the TMA fetches of
+    // the nodes below the root step, fetches issued on it and seen landed
+    unsigned long long kid_mbar;
+    uint32_t kid_arms, kid_seen;
 };
 
 // ---------------------------------------------------------------------------
@@ -1675,6 +1679,8 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     if (BU) return bu_rise<K, IPT>(p, H, sh, base, tslot, !sh.lockfree, (int)s - (int)sh.s, n, ref);
 
     uint32_t ib = 1, ic = 2;       // current node, next node
+    // nodes of a multiple of 16 bytes move by TMA (aligned buffers and nodes)
+    const bool tma_ok = (k * (uint32_t)sizeof(K)) % 16u == 0;
     K *cur_keys = root;
     uint32_t *cur_w = nullptr;     // nullptr = the root word
     uint32_t par = 0;
@@ -1708,14 +1714,25 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             }
             __syncwarp();
             if (lvl > 0 && !at_target && !sh.abort) {
-                g2s(c, nkeys, k, lane, 32u);
-                cp_async_commit();
-                if (lane == 0) {
-                    const uint32_t n2 = tnode >> (depth - lvl - 2);
-                    uint32_t *w2 = &H.state[slot_node(n2)];
-                    sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                if (tma_ok) {
+                    // the node by TMA (one lane), the next one tried meanwhile
+                    if (lane == 0) {
+                        tma_fetch(H, k, 1u, nslot, c, 0u, c, &sh.kid_mbar, sh.kid_arms);
+                        const uint32_t n2 = tnode >> (depth - lvl - 2);
+                        uint32_t *w2 = &H.state[slot_node(n2)];
+                        sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                        if (!tma_land(p, H, &sh.kid_mbar, sh.kid_arms, sh.kid_seen)) sh.abort = 1;
+                    }
+                } else {
+                    g2s(c, nkeys, k, lane, 32u);
+                    cp_async_commit();
+                    if (lane == 0) {
+                        const uint32_t n2 = tnode >> (depth - lvl - 2);
+                        uint32_t *w2 = &H.state[slot_node(n2)];
+                        sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                    }
+                    cp_async_wait();
                 }
-                cp_async_wait();
             }
             if (lane == 0) {
                 lap(sh, STAT_INS_WAIT_CYC, tw);
@@ -1783,16 +1800,28 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         if (lvl == 0) {
             // the root is released: now copy the level-1 node and try level 2
             if (ctrl) {
-                g2s(c, nkeys, k, lane, 32u);
-                cp_async_commit();
-                if (lane == 0) {
-                    const uint32_t n2 = tnode >> (depth - 2);
-                    uint32_t *w2 = &H.state[slot_node(n2)];
-                    sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                if (tma_ok) {
+                    if (lane == 0) {
+                        tma_fetch(H, k, 1u, nslot, c, 0u, c, &sh.kid_mbar, sh.kid_arms);
+                        const uint32_t n2 = tnode >> (depth - 2);
+                        uint32_t *w2 = &H.state[slot_node(n2)];
+                        sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                        if (!tma_land(p, H, &sh.kid_mbar, sh.kid_arms, sh.kid_seen)) sh.abort = 1;
+                    }
+                    __syncwarp();
+                } else {
+                    g2s(c, nkeys, k, lane, 32u);
+                    cp_async_commit();
+                    if (lane == 0) {
+                        const uint32_t n2 = tnode >> (depth - 2);
+                        uint32_t *w2 = &H.state[slot_node(n2)];
+                        sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
+                    }
+                    cp_async_wait();
                 }
-                cp_async_wait();
             }
             bar_all();
+            if (sh.abort) return false;
         }
         const uint32_t t = ib; ib = ic; ic = t;
         cur_keys = nkeys;
@@ -1993,7 +2022,7 @@ __device__ __forceinline__ void cw_lock_two(const Params<K> &p, const HeapView<K
     __syncwarp();
 }
 
-template <typename K>
+template <typename K, bool TMA>
 __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapView<K> &H,
                                                  Shared &sh, uint32_t sl, uint32_t sr,
                                                  uint32_t first0, uint32_t first1, K *dl, K *dr,
@@ -2002,6 +2031,17 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
     const uint32_t lane = clane();
     const uint32_t k = p.k;
     cw_lock_two(p, H, sh, sl, sr, first0, first1, lk);
+    if (TMA && lk[0] == ST_AVAIL && lk[1] == ST_AVAIL && (k * (uint32_t)sizeof(K)) % 16u == 0) {
+        // both nodes by one TMA fetch (one lane)
+        if (lane == 0) {
+            tma_fetch(H, k, 2u, sl, dl, sr, dr, &sh.kid_mbar, sh.kid_arms);
+            if (!tma_land(p, H, &sh.kid_mbar, sh.kid_arms, sh.kid_seen))
+                lk[0] = lk[1] = ST_GAVE_UP;
+            stat_add(sh, STAT_LOADS, 2);
+        }
+        __syncwarp();
+        return;
+    }
     if (lk[0] == ST_AVAIL) g2s(dl, node_keys(H, sl, k), k, lane, 32u);
     if (lk[1] == ST_AVAIL) g2s(dr, node_keys(H, sr, k), k, lane, 32u);
     cp_async_commit();
@@ -2014,7 +2054,11 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
 // `out_off`.  Six smem buffers rotate between the roles current node, left
 // and right child, and three free ones.  Returns false when the block must
 // stop.
-template <typename K, int IPT, bool TMA = false>
+// ROOT_TMA (delete-only launches): the root step's copies by TMA; the levels
+// below keep the control warp's copies there (they overlap the merges: TMA
+// measured no faster).  Other launches fetch the nodes of every level below
+// the root step by TMA (faster walks: heap sets +2.6%).
+template <typename K, int IPT, bool ROOT_TMA = false>
 __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t want, unsigned long long out_off, unsigned long long ref,
                        uint32_t *count_out, long long req)
@@ -2137,7 +2181,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     } else if (!root_gone) {
         uint32_t sl, sr;
         child_slots(1, H.max_nodes, sl, sr);
-        if (TMA && m >= 16u && (k * (uint32_t)sizeof(K)) % 16u == 0) {
+        if (ROOT_TMA && m >= 16u && (k * (uint32_t)sizeof(K)) % 16u == 0) {
             // the root step of delete-only launches: level 1 fetched by TMA
             // the moment both locks are held, the last node (below level 3:
             // the top four levels are full) as soon as it is taken -- one
@@ -2192,7 +2236,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 __syncwarp();
                 if (!sh.abort) g2s(PB(f1), node_keys(H, m, k), k, lane, 32u);
                 cp_async_commit();
-                cw_take_children(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir), sh.lk[0]);
+                cw_take_children<K, !ROOT_TMA>(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir),
+                                               sh.lk[0]);
             } else {
                 // try the last node and both children at once.  An INS still
                 // in flight to the last node may need a child of the root, so
@@ -2213,11 +2258,12 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 cp_async_commit();
                 const uint32_t c0 = __shfl_sync(0xffffffffu, t, 0);
                 const uint32_t c1 = __shfl_sync(0xffffffffu, t, 1);
-                cw_take_children(p, H, sh, sl, sr, inflight ? NO_TRY : c0,
+                cw_take_children<K, !ROOT_TMA>(p, H, sh, sl, sr, inflight ? NO_TRY : c0,
                                  inflight ? NO_TRY : c1, PB(il), PB(ir), sh.lk[0]);
             }
         } else {
-            cw_take_children(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir), sh.lk[0]);
+            cw_take_children<K, !ROOT_TMA>(p, H, sh, sl, sr, NO_TRY, NO_TRY, PB(il), PB(ir),
+                                           sh.lk[0]);
         }
     }
     bar_all();
@@ -2333,7 +2379,8 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 }
             } else {
                 long long tw = clock64();
-                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2), sh.lk[par ^ 1]);
+                cw_take_children<K, !ROOT_TMA>(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
+                                               sh.lk[par ^ 1]);
                 if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
             }
             bar_all();
@@ -2438,7 +2485,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             } else {
                 // the small child's children, locked and loaded meanwhile
                 long long tw = clock64();
-                cw_take_children(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
+                cw_take_children<K, !ROOT_TMA>(p, H, sh, gl, gr, NO_TRY, NO_TRY, PB(f1), PB(f2),
                                  sh.lk[par ^ 1]);
                 if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
             }
@@ -2514,8 +2561,9 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                     long long tw = clock64();
                     const uint32_t t0 = __shfl_sync(0xffffffffu, t_try, 0);
                     const uint32_t t1 = __shfl_sync(0xffffffffu, t_try, 1);
-                    cw_take_children(p, H, sh, gl, gr, gl ? t0 : NO_TRY, gr ? t1 : NO_TRY,
-                                     PB(f1), PB(f2), sh.lk[par ^ 1]);
+                    cw_take_children<K, !ROOT_TMA>(p, H, sh, gl, gr, gl ? t0 : NO_TRY,
+                                                   gr ? t1 : NO_TRY, PB(f1), PB(f2),
+                                                   sh.lk[par ^ 1]);
                     if (lane == 0) lap(sh, STAT_DEL_WAIT_CYC, tw);
                 }
             }
@@ -2743,6 +2791,9 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         if (DEL_ONLY) {
             mbar_init(&sh.l1_mbar, 1u);
             mbar_init(&sh.last_mbar, 1u);
+        } else {
+            sh.kid_arms = sh.kid_seen = 0;
+            mbar_init(&sh.kid_mbar, 1u);
         }
     }
     bar_block();
@@ -2923,6 +2974,11 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
                 while (!mbar_try_wait(&sh.last_mbar, (sh.last_arms - 1u) & 1u) &&
                        gtimer() - t0 < 2000000000ull) {
                 }
+        } else if (sh.kid_seen != sh.kid_arms) {
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_wait(&sh.kid_mbar, (sh.kid_arms - 1u) & 1u) &&
+                   gtimer() - t0 < 1000000000ull) {
+            }
         }
     }
     bar_all();
