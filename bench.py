@@ -44,12 +44,12 @@ UNIT = "keys/s"
 # removed) has these SHA-256 digests; reported as null once the code differs.
 MEASURED_TRAFFIC = {
     "sources": {
-        "gheap_kernel.cuh": "671431842c35851108088e880ff6ba340056bff3943a392d6a9d94f592c72b5a",
+        "gheap_kernel.cuh": "05b381a2ee9f93e88b494b0abadc67d6e3e78d82009c6c6a2ee4e8e3d7e3caa5",
         "gheap.cu": "c39b69e063f8d7e9c0b99a1d8490a9f7f557344e6c00e25f17bcef618ed629cc",
     },
     "bottom_up": True,
-    "insert": 706652672 + 748828928,
-    "delete": 1160636416 + 1424844288,
+    "insert": 706596096 + 748616960,
+    "delete": 1163938816 + 1425162240,
 }
 
 
