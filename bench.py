@@ -314,15 +314,18 @@ def run_reference(args):
             dist.destroy_process_group()
             return
     n_sample = 1 << 23
-    vals = []
+    vals, secs = [], []
     for i in range(args.warmup + args.steps):
         v, dt = cpu_oracle_sample(n_sample)
         if i >= args.warmup:
             vals.append(v)
+            secs.append(dt)
     value = float(np.median(vals))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        # a step is the bounded sample (config.sample_keys keys in and out)
+        "ms_per_step": float(np.median(secs)) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": "insert-all + deleteMin-all, 2^26 uniform u32 keys, k=1024",
