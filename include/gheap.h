@@ -115,12 +115,14 @@ int heap_set_timeout(gheap_t h, uint64_t ns);
 int heap_set_stats(gheap_t h, uint32_t on);
 
 /* INS/DEL cooperation (Section 3.3.2): a DEL whose last node is the target of
- * an INS still on its way down may mark that target and wait, holding the
- * root, until the INS delivers its keys there -- the paper's protocol, n = 0.
- * With n > 0 (default 64) the DEL first hands the root back and queues again
- * up to n times, so that the operations behind it proceed while the INS
- * lands; only the root order changes, never what a DEL returns for its place
- * in that order. */
+ * an INS still on its way down marks that target and waits, holding the
+ * root, until the INS delivers its keys -- the paper's protocol, n = 0 (the
+ * default).  The INS checks its target at every level and, once marked,
+ * hands over the keys it carries after the level it is on, so the wait is
+ * one level step.  With n > 0 the DEL first hands the root back and queues
+ * again up to n times, so that the operations behind it proceed meanwhile;
+ * only the root order changes, never what a DEL returns for its place in
+ * that order. */
 int heap_set_yields(gheap_t h, uint32_t n);
 
 /* Inserts n keys (Section 3.2.2 top-down INS, Section 3.3.2 partial
@@ -191,7 +193,7 @@ int heap_geometry(gheap_t h, uint64_t *max_nodes, uint32_t *k,
  * (Section 4.3).  The map is its own inverse. */
 uint64_t heap_slot_to_node(uint64_t j);
 
-/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 23:
+/* Device counters when created with GHEAP_FLAG_STATS (synchronizes), n <= 24:
  * out[0] node loads, out[1] node stores, out[2] merges, out[3] merges skipped
  * as disjoint (Section 4.3), out[4] INS ops, out[5] DEL ops, out[6] lock
  * waits that spun, out[7] sum of root-hold time in ns; then SM cycles seen
@@ -202,7 +204,9 @@ uint64_t heap_slot_to_node(uint64_t j);
  * [18], INS levels [19]; DELs that received the keys of an INS whose target
  * they had marked (Section 3.3.2) [20], root hand-backs of DELs waiting for
  * such an INS (heap_set_yields) [21], children a DEL found reserved as the
- * target of an INS still on its way down and treated as absent [22]. */
+ * target of an INS still on its way down and treated as absent [22], INSs
+ * that handed their keys to a DEL that had marked their target, at the
+ * level they were on, instead of carrying them to it [23]. */
 int heap_get_stats(gheap_t h, uint64_t *out, uint32_t n);
 
 /* Test hook for the bounded waits: marks the root lock as held, with no

@@ -29,7 +29,7 @@ STAT_NAMES = ("node_loads", "node_stores", "merges", "merges_skipped", "ins_ops"
               "del_acquire_cyc", "del_root_step_cyc", "del_child_wait_cyc",
               "del_child_load_cyc", "del_merge_cyc", "del_store_release_cyc", "del_levels",
               "ins_acquire_cyc", "ins_sort_cyc", "ins_wait_cyc", "ins_step_cyc", "ins_levels",
-              "deliveries", "del_yields", "target_children")
+              "deliveries", "del_yields", "target_children", "intercepts")
 
 _lib = None
 
