@@ -44,12 +44,12 @@ UNIT = "keys/s"
 # removed) has these SHA-256 digests; reported as null once the code differs.
 MEASURED_TRAFFIC = {
     "sources": {
-        "gheap_kernel.cuh": "05b381a2ee9f93e88b494b0abadc67d6e3e78d82009c6c6a2ee4e8e3d7e3caa5",
+        "gheap_kernel.cuh": "2794e98210d9bde89f498d1cdd33532c44ab69de1af5907be7a305bcff247596",
         "gheap.cu": "c39b69e063f8d7e9c0b99a1d8490a9f7f557344e6c00e25f17bcef618ed629cc",
     },
     "bottom_up": True,
-    "insert": 706596096 + 748616960,
-    "delete": 1163938816 + 1425162240,
+    "insert": 709083904 + 749606912,
+    "delete": 1163749376 + 1426071552,
 }
 
 
