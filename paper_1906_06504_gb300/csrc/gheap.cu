@@ -1028,6 +1028,10 @@ namespace {
 
 enum : uint8_t { RQ_FREE = 0, RQ_INFLIGHT = 1, RQ_DONE = 2, RQ_TAKEN = 3 };
 
+// The native serving loop's completion scan ends after this many requests in
+// a row still running (ring_poll).
+constexpr uint64_t POLL_RUN = 512;
+
 struct RingReq {
     uint64_t seq;
     uint64_t op_end;                 // ring position after its last op
@@ -1327,6 +1331,34 @@ void ring_publish(gheap_ring_t r)
     __atomic_store_n(r->tail, (unsigned long long)r->op_tail, __ATOMIC_RELEASE);
 }
 
+// Marks completed and reports up to `max` requests in submission order,
+// scanning from the oldest one in flight; the scan ends after `run` requests
+// in a row that are still running (the ring runs operations in order, so
+// the finished ones are mostly the oldest; a later one is found by a later
+// call).  Returns the count.
+uint32_t ring_poll(gheap_ring_t r, uint64_t *ids, uint64_t *counts, int32_t *status, uint32_t max,
+                   uint64_t run)
+{
+    uint32_t c = 0;
+    uint64_t busy = 0;
+    for (uint64_t s = r->oldest; s < r->next_seq && c < max && busy < run; s++) {
+        const uint32_t slot = (uint32_t)(s % r->n_slots);
+        RingReq &q = r->reqs[slot];
+        if (q.state != RQ_INFLIGHT) continue;
+        if (__atomic_load_n(&r->done[slot].seq, __ATOMIC_ACQUIRE) != s + 1) {
+            busy++;
+            continue;
+        }
+        busy = 0;
+        q.state = RQ_DONE;
+        ids[c] = s;
+        if (counts) counts[c] = q.kind == GHEAP_OP_DEL ? r->done[slot].count : q.n;
+        if (status) status[c] = status_code(r->done[slot].status);
+        c++;
+    }
+    return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1358,19 +1390,7 @@ int heapring_poll(gheap_ring_t r, uint64_t *ids, uint64_t *counts, int32_t *stat
                   uint32_t *n_done)
 {
     if (!r || !n_done || (max && !ids)) return GHEAP_ERR_ARG;
-    uint32_t c = 0;
-    for (uint64_t s = r->oldest; s < r->next_seq && c < max; s++) {
-        const uint32_t slot = (uint32_t)(s % r->n_slots);
-        RingReq &q = r->reqs[slot];
-        if (q.state != RQ_INFLIGHT) continue;
-        if (__atomic_load_n(&r->done[slot].seq, __ATOMIC_ACQUIRE) != s + 1) continue;
-        q.state = RQ_DONE;
-        ids[c] = s;
-        if (counts) counts[c] = q.kind == GHEAP_OP_DEL ? r->done[slot].count : q.n;
-        if (status) status[c] = status_code(r->done[slot].status);
-        c++;
-    }
-    *n_done = c;
+    *n_done = ring_poll(r, ids, counts, status, max, UINT64_MAX);
     return GHEAP_OK;
 }
 
@@ -1485,7 +1505,9 @@ int heapring_serve(gheap_ring_t r, uint64_t n_req, const double *arrival, const 
         }
         // completions: take each deleteMin's keys into its place
         uint32_t nd = 0;
-        heapring_poll(r, ids.data(), counts.data(), sts.data(), r->n_slots, &nd);
+        // with many requests in flight a full scan of them on every pass
+        // would cost more than the completions it finds
+        nd = ring_poll(r, ids.data(), counts.data(), sts.data(), r->n_slots, POLL_RUN);
         now = now_s();
         for (uint32_t j = 0; j < nd; j++) {
             const uint64_t i = req_of[ids[j] - base];
