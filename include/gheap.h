@@ -271,7 +271,7 @@ int heapset_unbind(gheapset_t s, uint32_t i, void *stream);
 
 /* The set's operation counters (created with GHEAP_FLAG_STATS), summed over
  * every launch on the set, in the order and meaning of heap_get_stats; n <=
- * 20 (synchronizes). */
+ * 24 (synchronizes). */
 int heapset_get_stats(gheapset_t s, uint64_t *out, uint32_t n);
 
 /* Launch shape and wait bound, as heap_set_launch / heap_set_timeout, except
@@ -285,7 +285,11 @@ int heapset_set_timeout(gheapset_t s, uint64_t ns);
  * ascending, to d_out_keys[offset..] and its count to d_out_counts[i]
  * (INS: n, or 0 when skipped).  An op whose heap already holds a sticky
  * error is skipped; an insert beyond a heap's node storage sets that heap's
- * GHEAP_ERR_FULL.  Capacities are not checked on the host. */
+ * GHEAP_ERR_FULL.  Capacities are not checked on the host.  With d_in_keys
+ * NULL (and d_out_keys given) the list must hold only DELs: it runs the
+ * delete-only specialisation of the kernel (one block per SM, the root
+ * step's node fetches by TMA), and an INS in it sets its heap's
+ * GHEAP_ERR_STATE while the other heaps go on. */
 int heapset_ops(gheapset_t s, const gheapset_op *d_ops, uint64_t n_ops, const void *d_in_keys,
                 void *d_out_keys, uint32_t *d_out_counts, void *stream);
 

@@ -87,8 +87,12 @@ struct Shape {
 template <typename K, int IPT>
 int launch_t(const Shape &sp, gh::Params<K> &p, uint64_t n_ops, cudaStream_t s)
 {
+    // a heap-set list with no input keys holds only DELs (an INS there is its
+    // heap's sticky error): the delete-only walk, ops naming their heaps
     auto kern = p.mode == gh::MODE_DELETE ? gh::heap_kernel<K, IPT, true>
-                                          : gh::heap_kernel<K, IPT, false>;
+                : (p.mode == gh::MODE_SET && p.in == nullptr && p.out != nullptr)
+                    ? gh::heap_kernel<K, IPT, true, true>
+                    : gh::heap_kernel<K, IPT, false>;
     const uint32_t threads = threads_for(sp.k, IPT);
     const size_t smem = 6u * (size_t)sp.k * sizeof(K);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -322,6 +322,19 @@ __device__ __forceinline__ void bar_mg()
     asm volatile("bar.sync 1, %0;" :: "r"(blockDim.x - 64u) : "memory");
 }
 
+// Merge threads only, with an OR of `v` over them (named barrier 1): the
+// same result in every merge thread.
+__device__ __forceinline__ bool bar_mg_or(bool v)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 p, %1, 0;\n\t"
+                 "bar.red.or.pred q, 1, %2, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v), "r"(blockDim.x - 64u) : "memory");
+    return r != 0;
+}
+
 // Every thread of the block, release warp included (named barrier 2).
 __device__ __forceinline__ void bar_block()
 {
@@ -2090,7 +2103,46 @@ __device__ __forceinline__ void cw_take_children(const Params<K> &p, const HeapV
 // below keep the control warp's copies there (they overlap the merges: TMA
 // measured no faster).  Other launches fetch the nodes of every level below
 // the root step by TMA (faster walks: heap sets +2.6%).
-template <typename K, int IPT, bool ROOT_TMA = false>
+// DEL root step of delete-only launches, merge threads, when keys of the root
+// and the partial buffer are left over (tn of them, in `left`): waits
+// (bounded) for the fetch of the last node into `last` (phase parity `par`
+// of the last-node mbarrier), then MergeAndSort(left-over, last node): the k
+// smallest become the new root in `root_buf`, the rest the partial buffer.
+// A control warp that gave up on the last node has set abort, which ends the
+// wait; the merge threads then decide together to skip the merge (the
+// operation fails).  Kept out of line: the path without left-over keys stays
+// as short as it was.
+template <typename K, int IPT>
+__device__ __noinline__ void del_early_refill(Shared &sh, Hdr *hdr, K *buf,
+                                              unsigned long long timeout_ns, uint32_t k,
+                                              uint32_t par, K *left, uint32_t tn, K *last,
+                                              K *root_buf)
+{
+    const unsigned long long t0 = gtimer();
+    bool miss = false;
+    while (!mbar_try_wait(&sh.last_mbar, par)) {
+        if (*(volatile int *)&sh.abort) {
+            miss = true;
+            break;
+        }
+        if (gtimer() - t0 > timeout_ns) {
+            atomicCAS(&hdr->err, E_NONE, E_TIMEOUT);
+            sh.abort = 1;
+            miss = true;
+            break;
+        }
+    }
+    if (!bar_mg_or(miss)) {
+        merge_split<K, IPT>(left, tn, last, k, root_buf, k, left);
+        s2g(buf, left, tn);
+    }
+}
+
+// EARLY (delete-only heap-set launches, whose heaps mostly hold a partial
+// buffer): the root step's refill from the last node runs out of line as soon
+// as that node has landed (del_early_refill).  Not built into the single-heap
+// delete-only kernel, whose deleteMin-all measured 1% slower for carrying it.
+template <typename K, int IPT, bool ROOT_TMA = false, bool EARLY = false>
 __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *base,
                        uint32_t want, unsigned long long out_off, unsigned long long ref,
                        uint32_t *count_out, long long req)
@@ -2100,6 +2152,10 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     const uint32_t lane = clane();
     K *root = node_keys(H, 1u, k);
     long long tp = clock64();
+    // phase parity of this operation's fetch of the last node (the fetch is
+    // issued after the next barrier, so the count read here is the previous
+    // operations')
+    const uint32_t last_par = EARLY ? (sh.last_arms & 1u) : 0u;
 #define PB(i) (base + (size_t)(i) * k)
 
     // ---- take the root, the ticket and the output range
@@ -2192,6 +2248,11 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     const bool root_gone = s < take && m == 1;
     const uint32_t tn = k - take + s;             // root + buffer keys left (when s < take)
     uint32_t ic = 0, il = 1, ir = 2, f1 = 3, f2 = 4;   // buffer 5 holds the partial buffer
+    // the root step's fetches (below): with keys left over from the root and
+    // the buffer, the refill MergeAndSort(left-over, last node) runs as soon
+    // as the last node has landed, while level 1 is still awaited
+    const bool early = EARLY && ROOT_TMA && need_last && tn > 0 && m >= 16u &&
+                       (k * (uint32_t)sizeof(K)) % 16u == 0;
 
     // ---- root step.  Merge threads: root and buffer in, output, first part
     // of the refill.  Control warp: the last node, then the root's children.
@@ -2210,6 +2271,9 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             merge_split<K, IPT>(PB(ic) + take, k - take, PB(5), s, PB(5), tn, PB(5));
             if (root_gone) s2g(H.buf, PB(5), tn);
         }
+        if (early)
+            del_early_refill<K, IPT>(sh, H.hdr, H.buf, p.timeout_ns, k, last_par, PB(5), tn,
+                                     PB(f1), PB(ic));
     } else if (!root_gone) {
         uint32_t sl, sr;
         child_slots(1, H.max_nodes, sl, sr);
@@ -2312,7 +2376,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     if (need_last) {
         nm = m - 1;
         if (tn > 0) {
-            if (!ctrl) {
+            if (!ctrl && !early) {
                 merge_split<K, IPT>(PB(5), tn, PB(f1), k, PB(ic), k, PB(5));
                 s2g(H.buf, PB(5), tn);
             }
@@ -2322,7 +2386,7 @@ __device__ bool del_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         }
         if (!ctrl && threadIdx.x == 0) stat_add(sh, STAT_LOADS, 1);
     }
-    if (need_last && tn > 0) bar_all();   // the merge above rewrote PB(ic)
+    if (need_last && tn > 0 && !early) bar_all();   // the merge above rewrote PB(ic)
     if (ctrl && lane == 0) lap(sh, STAT_DEL_ROOT_CYC, tp);
 
     // ---- sift down (Section 3.2.1).  At the top of every level the block
@@ -2793,7 +2857,11 @@ struct MaxThreads { static constexpr int value = IPT >= 8 ? 320 : 576; };
 template <int IPT, bool DEL_ONLY>
 struct MinBlocks { static constexpr int value = (DEL_ONLY || IPT < 8) ? 1 : 2; };
 
-template <typename K, int IPT, bool DEL_ONLY>
+// SET_DEL (with DEL_ONLY): the delete-only specialisation for heap-set
+// launches whose operation list carries no input keys (MODE_SET, every
+// operation a DEL): each operation names its heap as in the general kernel,
+// and the walk is the delete-only one.
+template <typename K, int IPT, bool DEL_ONLY, bool SET_DEL = false>
 __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ONLY>::value))
     heap_kernel(Params<K> p)
 {
@@ -2805,7 +2873,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
     const uint32_t k = p.k;
     K *base = reinterpret_cast<K *>(smem_raw);   // 6 node buffers
     const bool ring = !DEL_ONLY && p.mode == MODE_RING;
-    const bool multi = !DEL_ONLY && (p.mode == MODE_SET || ring);
+    const bool multi = SET_DEL || (!DEL_ONLY && (p.mode == MODE_SET || ring));
     const HeapView<K> &H = multi ? set_view : p.h;
     __shared__ uint32_t ring_req;      // MODE_RING: request slot of the current op
     // a heap-set launch holding only inserts inserts bottom-up (no DEL can
@@ -2840,7 +2908,7 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         p.n = nd < p.n ? nd : p.n;
     }
     unsigned long long n_ops;
-    if (!DEL_ONLY && (p.mode == MODE_OPS || multi)) n_ops = p.n_ops;
+    if (SET_DEL || (!DEL_ONLY && (p.mode == MODE_OPS || multi))) n_ops = p.n_ops;
     else n_ops = (p.n + k - 1) / k;
 
     for (;;) {
@@ -2878,8 +2946,10 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
                 // error are skipped; a malformed op is its heap's sticky error
                 set_skip = d.heap >= p.n_heaps || set_view.hdr == nullptr;
                 if (!set_skip) {
+                    // (a delete-only launch has no input keys for an INS)
                     const bool bad = set_n > k || (set_cursor && (set_kind != GHEAP_OP_DEL ||
-                                                                  p.req_cursor == nullptr));
+                                                                  p.req_cursor == nullptr)) ||
+                                     (SET_DEL && set_kind != GHEAP_OP_DEL);
                     if (bad) set_err(set_view, E_STATE);
                     set_skip = bad || ld_relaxed(&set_view.hdr->err) != E_NONE;
                 }
@@ -2897,15 +2967,15 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         bool ok;
         uint32_t kind, n;
         unsigned long long off;
-        if (DEL_ONLY) {
+        if (DEL_ONLY && !SET_DEL) {
             kind = GHEAP_OP_DEL;
             n = k;
             off = 0;
-        } else if (p.mode == MODE_INSERT) {
+        } else if (!DEL_ONLY && p.mode == MODE_INSERT) {
             kind = GHEAP_OP_INS;
             off = op * k;
             n = (uint32_t)min((unsigned long long)k, p.n - off);
-        } else if (p.mode == MODE_DELETE) {
+        } else if (!DEL_ONLY && p.mode == MODE_DELETE) {
             kind = GHEAP_OP_DEL;
             n = k;
             off = 0;
@@ -2930,7 +3000,12 @@ __global__ void __launch_bounds__(MaxThreads<IPT>::value, (MinBlocks<IPT, DEL_ON
         }
         const bool listed = !DEL_ONLY && (p.mode == MODE_OPS || multi);
         if constexpr (DEL_ONLY) {
-            ok = del_op<K, IPT, true>(p, H, sh, base, n, off, op, nullptr, -1ll);
+            if constexpr (SET_DEL)
+                ok = del_op<K, IPT, true, true>(p, H, sh, base, n, off, op,
+                                                p.out_counts ? p.out_counts + op : nullptr,
+                                                set_cursor ? (long long)off : -1ll);
+            else
+                ok = del_op<K, IPT, true>(p, H, sh, base, n, off, op, nullptr, -1ll);
             if (threadIdx.x == 0) stat_add(sh, STAT_DEL, 1);
         } else if (kind == GHEAP_OP_INS) {
             // stage and sort the batch before taking the root (Section 4.1)

@@ -200,6 +200,86 @@ def test_heapset_graph_replay_matches_direct(bottom_up):
                 assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("k,key_bytes", [(1024, 4), (2048, 4), (256, 8)])
+def test_heapset_delete_only_launch(k, key_bytes):
+    """A list with no input keys runs the delete-only walk (the root step's
+    fetches included, on heaps of 16 nodes and more): after a prefill, random
+    DELs of 1..k keys over heaps of uneven sizes, more than some heaps hold;
+    every DEL equals the replay of its heap's record, the per-op counts
+    included, and the heaps keep Properties 1-3.  An INS in a list with no
+    input keys is its heap's sticky error; the other heaps go on."""
+    rng = np.random.default_rng(900 + k + key_bytes)
+    dt = np_dtype(key_bytes)
+    sizes = np.array([60 * k + 17, 5 * k, 300 * k + 3, 33, 40 * k, 128 * k])
+    keys = rng.integers(0, np.iinfo(dt).max, int(sizes.sum()), dtype=dt, endpoint=True)
+    with GHeapSet([int(c) for c in sizes], k=k, key_bytes=key_bytes, log_capacity=2048) as hs:
+        run = SetRun(hs)
+        run.launch(inputs.set_phase_ops(sizes, k, OP_INS), keys, 0)
+        n_ops = 900
+        heap = rng.integers(0, sizes.size, n_ops)
+        n = rng.integers(1, k + 1, n_ops)
+        ops = np.zeros(n_ops, dtype=[("heap", "<u4"), ("kind_n", "<u4"), ("offset", "<u8")])
+        ops["heap"] = heap
+        ops["kind_n"] = (OP_DEL << 24) | n
+        ops["offset"] = np.concatenate([[0], np.cumsum(n)[:-1]])
+        out, counts = run.launch(ops, np.empty(0, dt), int(n.sum()))
+        assert run.replay() == n_ops
+        c = counts.cpu().numpy()
+        assert (c <= n).all() and c.sum() == sizes.sum() - sum(h.size() for h in hs.heaps)
+        for h in hs.heaps:
+            check_properties(h)
+        # an INS among the DELs of a list with no input keys
+        bad = np.zeros(3, dtype=ops.dtype)
+        bad["heap"] = [0, 2, 4]
+        bad["kind_n"] = [(OP_DEL << 24) | 5, (OP_INS << 24) | 5, (OP_DEL << 24) | 5]
+        bad["offset"] = [0, 0, 5]
+        before = [h.size() for h in hs.heaps]
+        o = torch.zeros(16, dtype=torch.int32 if key_bytes == 4 else torch.int64, device="cuda")
+        hs.ops(torch.from_numpy(bad.view(np.uint8).copy()).cuda(), None, o)
+        assert hs.heaps[2].sync_code() == -6
+        assert hs.heaps[0].sync_code() == 0 and hs.heaps[4].sync_code() == 0
+        assert hs.heaps[0].size() == max(before[0] - 5, 0)
+        assert hs.heaps[4].size() == max(before[4] - 5, 0)
+
+
+def test_heapset_delete_only_request_cursors():
+    """Delete-only list through heapset_ops_req: the DELs of one request fill
+    its output range contiguously in the order they hold their heap's root,
+    and the request's cursor ends at the keys it got."""
+    k = 1024
+    sizes = np.array([40 * k, 9 * k + 100, 70 * k])
+    keys = inputs.keys_u32(inputs.config_seed(5) + 21, int(sizes.sum()))
+    reqs = [(0, 5 * k + 3), (2, 3 * k), (1, 12 * k), (0, 700), (2, 2 * k + 1)]
+    ops, bases, pos = [], [], 0
+    for r, (h, want) in enumerate(reqs):
+        bases.append(pos)
+        pos += want
+        for j in range(0, want, k):
+            ops.append((h, (OP_DEL << 24) | (1 << 23) | min(k, want - j), r))
+    ops = np.array(ops, dtype=[("heap", "<u4"), ("kind_n", "<u4"), ("offset", "<u8")])
+    with GHeapSet([int(c) for c in sizes], k=k) as hs:
+        SetRun(hs).launch(inputs.set_phase_ops(sizes, k, OP_INS), keys, 0)
+        hs.sync()
+        # one block: the operations take their heaps' roots in list order
+        hs.set_launch(ctas=1)
+        out = torch.zeros(pos, dtype=torch.int32, device="cuda")
+        req_base = torch.tensor(bases, dtype=torch.int64, device="cuda")
+        cursor = torch.zeros(len(reqs), dtype=torch.int64, device="cuda")
+        hs.ops_req(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), None, out, None,
+                   req_base, cursor)
+        hs.sync()
+        got = to_host(out, 4)
+        cur = cursor.cpu().numpy()
+        base = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        left = {h: np.sort(keys[base[h]:base[h] + sizes[h]]) for h in range(sizes.size)}
+        for r, (h, want) in enumerate(reqs):
+            # each request gets the next smallest keys of its heap
+            take = min(want, left[h].size)
+            assert cur[r] == take
+            assert np.array_equal(got[bases[r]:bases[r] + take], left[h][:take])
+            left[h] = left[h][take:]
+
+
 def test_heapset_error_is_per_heap():
     """A heap whose root lock never frees times out; the other heaps of the
     same launch finish correctly."""
