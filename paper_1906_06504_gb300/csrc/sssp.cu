@@ -10,7 +10,10 @@
 // vertices of more than HEAVY out-edges are queued for sssp_relax_heavy,
 // which spreads each one over the whole grid.  The last block of
 // sssp_relax_heavy keeps the device's count of live heap keys and reports it
-// to the iteration driver of app_loop.cuh.
+// to the iteration driver of app_loop.cuh.  On a graph with no vertex of
+// more than HEAVY out-edges (checked at each run) the iteration has three
+// steps: sssp_relax takes every popped key and its last block does the
+// bookkeeping.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -126,15 +129,25 @@ __global__ void sssp_init(uint32_t *dist, uint32_t source, unsigned long long *f
     c->live = 1;
 }
 
-// Steps 2-3 of an iteration for the popped keys of degree <= HEAVY.
+__device__ void finish_iteration(Ctr *c, uint32_t par, unsigned long long cap,
+                                 unsigned long long *ring, uint32_t slot);
+
+// Steps 2-3 of an iteration for the popped keys of degree <= HEAVY (all of
+// them when `light`: the graph has no vertex above HEAVY out-edges, no
+// sssp_relax_heavy follows, and the last block to finish does the
+// iteration's bookkeeping; a vertex of more edges would still be relaxed,
+// by its block alone).
 __global__ void __launch_bounds__(RT) sssp_relax(Graph g, const unsigned long long *popped, Ctr *c,
                                                  uint32_t par, unsigned long long *front,
-                                                 unsigned long long cap, unsigned long long *heavy)
+                                                 unsigned long long cap, unsigned long long *heavy,
+                                                 uint32_t light, unsigned long long *ring,
+                                                 uint32_t slot)
 {
     __shared__ unsigned long long s_off[RT + 1];
     __shared__ unsigned long long s_beg[RT];
     __shared__ uint32_t s_d[RT];
     __shared__ unsigned long long s_warp[RT / 32];
+    __shared__ bool last;
     const unsigned long long np = c->popped;
     unsigned long long *n_front = &c->front[par];
     unsigned long long visited = 0, edges = 0, ins = 0;
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(RT) sssp_relax(Graph g, const unsigned long lo
                 visited++;
                 beg = g.rowptr[v];
                 deg = g.rowptr[v + 1] - beg;
-                if (deg > HEAVY) {
+                if (deg > HEAVY && !light) {
                     heavy[atomicAdd(&c->n_heavy, 1ull)] = key;
                     deg = 0;
                 }
@@ -190,6 +203,20 @@ __global__ void __launch_bounds__(RT) sssp_relax(Graph g, const unsigned long lo
         __syncthreads();
     }
     add_stats(c, visited, edges, ins);
+    if (light) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) last = atomicAdd(&c->done, 1ull) == gridDim.x - 1;
+        __syncthreads();
+        if (last && threadIdx.x == 0) finish_iteration(c, par, cap, ring, slot);
+    }
+}
+
+// Sets *flag when some vertex of [0, n) has more than HEAVY out-edges.
+__global__ void sssp_degree_check(const unsigned long long *rowptr, uint32_t n, uint32_t *flag)
+{
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (rowptr[v + 1] - rowptr[v] > HEAVY) atomicOr(flag, 1u);
 }
 
 // The iteration's bookkeeping (one thread, after every append of the
@@ -285,16 +312,18 @@ struct sssp_s {
     unsigned long long *d_heavy;    // high-degree keys of one iteration
     unsigned long long front_cap;
     Ctr *d_ctr;
+    uint32_t *d_flag;               // degree check: a vertex above HEAVY out-edges
     app::Loop loop;
     Graph key;                      // graph arrays the captured iterations use
     unsigned long long key_cap;
+    bool key_light;                 //   and whether they run without sssp_relax_heavy
 };
 
 namespace {
 
 // Enqueues one iteration: deleteMin, relax, relax of the heavy vertices and
 // the insert of the lowered keys.
-int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t par,
+int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, bool light, uint32_t par,
                       uint32_t slot, cudaStream_t st)
 {
     Ctr *c = s->d_ctr;
@@ -305,9 +334,11 @@ int enqueue_iteration(sssp_t s, const Graph &g, unsigned long long cap, uint32_t
     int rc = heap_delete_min(s->heap, s->d_batch, s->batch, reinterpret_cast<uint64_t *>(&c->popped),
                              st);
     if (rc != GHEAP_OK) return rc;
-    sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy);
-    sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy,
-                                               s->loop.d_ring, slot);
+    sssp_relax<<<relax_grid, RT, 0, st>>>(g, s->d_batch, c, par, s->d_front, cap, s->d_heavy,
+                                          light ? 1u : 0u, s->loop.d_ring, slot);
+    if (!light)
+        sssp_relax_heavy<<<heavy_grid, RT, 0, st>>>(g, c, par, s->d_front, cap, s->d_heavy,
+                                                   s->loop.d_ring, slot);
     if (cudaGetLastError() != cudaSuccess) return GHEAP_ERR_CUDA;
     return heap_insert_dev(s->heap, s->d_front, reinterpret_cast<const uint64_t *>(&c->front[par]),
                            cap, st);
@@ -332,6 +363,7 @@ int sssp_destroy(sssp_t s)
     cudaFree(s->d_front);
     cudaFree(s->d_heavy);
     cudaFree(s->d_ctr);
+    cudaFree(s->d_flag);
     delete s;
     return GHEAP_OK;
 }
@@ -361,7 +393,8 @@ int sssp_create(sssp_t *out, uint32_t n_vertices, uint64_t n_edges, uint32_t k, 
     bool ok = cudaMalloc(&s->d_batch, (size_t)batch * 8) == cudaSuccess &&
               cudaMalloc(&s->d_front, (size_t)s->front_cap * 8) == cudaSuccess &&
               cudaMalloc(&s->d_heavy, (size_t)batch * 8) == cudaSuccess &&
-              cudaMalloc(&s->d_ctr, sizeof(Ctr)) == cudaSuccess;
+              cudaMalloc(&s->d_ctr, sizeof(Ctr)) == cudaSuccess &&
+              cudaMalloc(&s->d_flag, sizeof(uint32_t)) == cudaSuccess;
     if (!ok) { sssp_destroy(s); return GHEAP_ERR_OOM; }
     rc = app::loop_init(s->loop);
     if (rc != GHEAP_OK) { sssp_destroy(s); return rc; }
@@ -394,17 +427,36 @@ int sssp_run(sssp_t s, const uint64_t *d_rowptr, const uint32_t *d_col, const ui
     g.dist = d_dist;
     const unsigned long long cap = n_edges ? n_edges : 1;
 
+    // a graph with no vertex above HEAVY out-edges runs its iterations
+    // without sssp_relax_heavy (synchronizes: the check is read here)
+    uint32_t heavy_flag = 0;
+    {
+        cudaError_t e = cudaMemsetAsync(s->d_flag, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+        const uint32_t blocks = (n_vertices + 255) / 256;
+        sssp_degree_check<<<blocks < (uint32_t)s->sm_count * 4 ? blocks : (uint32_t)s->sm_count * 4,
+                            256, 0, st>>>(g.rowptr, n_vertices, s->d_flag);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&heavy_flag, s->d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return GHEAP_ERR_CUDA;
+    }
+    const bool light = heavy_flag == 0;
+
     // the captured iterations bake in the graph arrays: capture again when
     // they change
     const bool same = app::loop_ready(s->loop) && s->key.rowptr == g.rowptr && s->key.col == g.col &&
-                      s->key.w == g.w && s->key.dist == g.dist && s->key_cap == cap;
+                      s->key.w == g.w && s->key.dist == g.dist && s->key_cap == cap &&
+                      s->key_light == light;
     if (!same) {
         const int rc = app::loop_capture(s->loop, [&](uint32_t par, uint32_t slot, cudaStream_t cs) {
-            return enqueue_iteration(s, g, cap, par, slot, cs);
+            return enqueue_iteration(s, g, cap, light, par, slot, cs);
         });
         if (rc != GHEAP_OK) return rc;
         s->key = g;
         s->key_cap = cap;
+        s->key_light = light;
     }
 
     int rc = heap_reset(s->heap, stream);
