@@ -67,8 +67,11 @@ gheap_t sssp_heap(sssp_t s);
 int sssp_set_launch(sssp_t s, uint32_t ctas, uint32_t items_per_thread);
 
 /* Computes dist[] from `source` on the context's stream and returns when it
- * is done (it synchronizes).  The graph must fit the sizes given at
- * creation; n_vertices here may be smaller.  `stats` (host, may be NULL)
+ * is done (it synchronizes, also once at the start to read a check of the
+ * graph's out-degrees: a graph with no vertex above 2048 out-edges runs each
+ * iteration without the kernel that spreads such vertices over the grid).
+ * The graph must fit the sizes given at creation; n_vertices here may be
+ * smaller.  `stats` (host, may be NULL)
  * receives the counters above.  Errors: ARG (source >= n_vertices, a null
  * pointer, sizes above the context's), FULL (more live keys than
  * heap_capacity), TIMEOUT, STATE, CUDA. */
