@@ -293,8 +293,12 @@ struct Shared {
     // the nodes below the root step, fetches issued on it and seen landed
     unsigned long long kid_mbar;
     uint32_t kid_arms, kid_seen;
-    int icpt;                 // top-down INS: a DEL marked the target; hand the keys over now
-    int icpt_held;            //   and the next node was already locked by the last try
+    // top-down INS, the control warp's decision for a level (0 go on, 1 hand
+    // the keys over to the target a DEL marked, 2 give up), by level parity:
+    // the merge threads read a level's word after its barrier, and the next
+    // word the control warp writes (at the top of the next level, before
+    // any barrier) is the other one
+    int ilvl[2];
 };
 
 // ---------------------------------------------------------------------------
@@ -1703,6 +1707,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
     K *cur_keys = root;
     uint32_t *cur_w = nullptr;     // nullptr = the root word
     uint32_t par = 0;
+    bool icpt_held = false;        // control lane 0: the next node was locked by the last try
     for (uint32_t lvl = 0;; ++lvl) {
         const uint32_t nxt = tnode >> (depth - lvl - 1);
         const uint32_t nslot = slot_node(nxt);
@@ -1721,28 +1726,29 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                 // marked it and waits: the keys carried after this level go
                 // to it at once instead of down the rest of the path (an
                 // insert-only launch has no DEL: no look at the target)
-                sh.icpt = p.mode != MODE_INSERT && lvl > 0 && !at_target &&
-                          ld_relaxed(&H.state[tslot]) == ST_MARKED;
-                sh.icpt_held = sh.icpt && v == ST_AVAIL;
+                int dec = (p.mode != MODE_INSERT && lvl > 0 && !at_target &&
+                           ld_relaxed(&H.state[tslot]) == ST_MARKED) ? 1 : 0;
+                icpt_held = dec == 1 && v == ST_AVAIL;
                 if (at_target) {
                     sh.deliver = (v == ST_MARKED);
                     if (v != ST_TARGET && v != ST_MARKED) {
                         set_err(H, E_STATE);
-                        sh.abort = 1;
+                        dec = 2;
                     }
-                } else if (sh.icpt) {
+                } else if (dec == 1) {
                     // the next node is not taken (only given back if the last
                     // level's try took it)
                 } else if (v != ST_AVAIL) {
                     v = lock_node(p, H, sh, nw, v);
                     if (v != ST_AVAIL) {
                         if (v != ST_GAVE_UP) set_err(H, E_STATE);
-                        sh.abort = 1;
+                        dec = 2;
                     }
                 }
+                sh.ilvl[par] = dec;
             }
             __syncwarp();
-            if (lvl > 0 && !at_target && !sh.abort && !sh.icpt) {
+            if (lvl > 0 && !at_target && sh.ilvl[par] == 0) {
                 if (tma_ok) {
                     // the node by TMA (one lane), the next one tried meanwhile
                     if (lane == 0) {
@@ -1750,7 +1756,8 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
                         const uint32_t n2 = tnode >> (depth - lvl - 2);
                         uint32_t *w2 = &H.state[slot_node(n2)];
                         sh.lk[par ^ 1][0] = (n2 == tnode) ? claim_target(w2) : try_lock(w2);
-                        if (!tma_land(p, H, &sh.kid_mbar, sh.kid_arms, sh.kid_seen)) sh.abort = 1;
+                        if (!tma_land(p, H, &sh.kid_mbar, sh.kid_arms, sh.kid_seen))
+                            sh.ilvl[par] = 2;
                     }
                 } else {
                     g2s(c, nkeys, k, lane, 32u);
@@ -1800,7 +1807,8 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             }
         }
         bar_all();
-        if (sh.abort) return false;
+        const int dec = sh.ilvl[par];
+        if (dec == 2) return false;
         // the root word and the level-1 node are released at once by the
         // control warp (the next operation waits for them); a node further
         // down goes back through the release warp, so that the control warp
@@ -1817,7 +1825,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
         } else if (threadIdx.x == 0) {
             post_step(p, H, sh, cur_w, nullptr, 0u, 0u);
         }
-        if (sh.icpt) {
+        if (dec == 1) {
             // deliver the carried keys to the marked target (Section 3.3.2's
             // hand-off, one level step after the mark instead of at the end
             // of the path): the nodes below were not touched
@@ -1827,7 +1835,7 @@ __device__ bool ins_op(const Params<K> &p, const HeapView<K> &H, Shared &sh, K *
             }
             bar_all();
             if (ctrl && lane == 0) {
-                if (sh.icpt_held) st_release(nw, ST_AVAIL);
+                if (icpt_held) st_release(nw, ST_AVAIL);
                 st_release(&H.state[tslot], ST_DELIVERED);
                 stat_add(sh, STAT_INTERCEPTS, 1);
             }
