@@ -152,7 +152,10 @@ int heap_delete_min(gheap_t h, void *d_out, uint64_t n, uint64_t *d_count,
  * insert/delete workload of Section 5.5).  d_ops: device array of n_ops
  * gheap_op.  max_insert_keys: the caller's bound on the keys the list
  * inserts, used for the capacity check.  d_out_counts: device uint32_t per
- * op (DEL: keys returned; INS: n), may be NULL. */
+ * op (DEL: keys returned; INS: n), may be NULL.  d_in_keys must be a valid
+ * device array when the list holds an INS, and d_out_keys when it holds a
+ * DEL: the operations are on the device, so the host cannot check this, and
+ * the kernel dereferences the pointer. */
 int heap_ops(gheap_t h, const gheap_op *d_ops, uint64_t n_ops,
              const void *d_in_keys, void *d_out_keys, uint32_t *d_out_counts,
              uint64_t max_insert_keys, void *stream);
@@ -285,7 +288,9 @@ int heapset_set_timeout(gheapset_t s, uint64_t ns);
  * ascending, to d_out_keys[offset..] and its count to d_out_counts[i]
  * (INS: n, or 0 when skipped).  An op whose heap already holds a sticky
  * error is skipped; an insert beyond a heap's node storage sets that heap's
- * GHEAP_ERR_FULL.  Capacities are not checked on the host.  With d_in_keys
+ * GHEAP_ERR_FULL.  Capacities are not checked on the host.  d_out_keys must
+ * be a valid device array when the list holds a DEL (the host cannot see
+ * the operations; the kernel dereferences it).  With d_in_keys
  * NULL (and d_out_keys given) the list must hold only DELs: it runs the
  * delete-only specialisation of the kernel (one block per SM, the root
  * step's node fetches by TMA), and an INS in it sets its heap's
